@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the EXX pair path on one GB300 (or N replicas under torchrun).
+
+Workload: 64 water-like molecules (256 orbitals) in a cubic 23.5 bohr cell on
+a 120^3 grid, R_pair / R_PE / R_ME = 8 / 6 / 8 bohr, 6th-order stencil, CG
+tolerance 1e-9, mixed FP32/FP64 path.  One step = one full EXX evaluation
+(pair list -> every pair's Poisson solve -> E_xx, D_xx, sigma_xx / Pi_xx)
+with the orbitals resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair Poisson solves/s and ms per EXX step (E_xx+D_xx+sigma_xx), %HBM roofline"
+UNIT = "pair_solves/s"
+WORKLOAD = ("water64_cubic23.5bohr_n120: 256 MLWFs, R_pair/R_PE/R_ME = 8/6/8 bohr, n = 3 (19-point stencil), "
+            "l_max = 6, CG tol 1e-9, mixed FP32/FP64")
+FALLBACK_HBM = 6800.0
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.samples = []
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in self.samples:
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profile_traffic(kernel_src_sha):
+    """DRAM bytes per launch of the pair solver from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for f in sorted(os.listdir(d)):
+        if not f.startswith("k_pair_solve") or not f.endswith(".md"):
+            continue
+        txt = open(os.path.join(d, f)).read()
+        m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+        m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+        if m_sha and m_b and m_sha.group(1) == kernel_src_sha:
+            return float(m_b.group(1))
+    return None
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "exx_dev.h", "kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2011_07209_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def algorithmic_bytes(n_pairs, total_iter, total_refine, n_pe, n_me, s):
+    """Bytes the pair solver must move per launch ("Algorithmic bytes"):
+    CG: 7 N_PE s per iteration (x, r, p read + written, p read by the stencil);
+    refinement: 3 N_PE 8 per FP64 residual (v, rho read, r written);
+    per pair: gather 2 N_ME 8, D read-modify-write 2 N_ME 16, rho 8 N_PE."""
+    return (total_iter * 7.0 * n_pe * s + total_refine * 3.0 * n_pe * 8.0
+            + n_pairs * (2.0 * n_me * 8.0 + 2.0 * n_me * 16.0 + 8.0 * n_pe))
+
+
+def cpu_baseline(ws, n_sample, seed=7209):
+    import numpy as np
+
+    import oracle
+    rows = oracle.pair_list(ws.lattice, ws.n, ws.centres, 8.0)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(rows), size=min(n_sample, len(rows)), replace=False)).astype(np.int32)
+    cores = os.cpu_count() or 1
+    p = oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, n_threads=cores)
+    t0 = time.perf_counter()
+    oracle.exx(ws, p, sel=sel, want_d=False)
+    dt = time.perf_counter() - t0
+    return {"value": len(sel) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} seeded pairs of the same workload (FP64 CG to 1e-9, OpenMP over pairs), "
+                      f"{dt:.1f} s wall"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import paper_2011_07209_gb300.synth as synth
+    ws = synth.make_config(2)
+    import numpy as np
+
+    import oracle
+    rows = oracle.pair_list(ws.lattice, ws.n, ws.centres, 8.0)
+    cores = os.cpu_count() or 1
+    p = oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, n_threads=cores)
+    rng = np.random.default_rng(7209)
+    per_step = max(cores, args.ref_sample)
+    times = []
+    for it in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(len(rows), size=per_step, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.exx(ws, p, sel=sel, want_d=False)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = per_step * len(times) / tot
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "pairs_per_step": per_step, "total_pairs_in_cell": int(len(rows)),
+                       "note": "each step is a bounded seeded sample of the cell's pairs"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} seeded pairs per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2011_07209_gb300.synth as synth
+    from paper_2011_07209_gb300 import driver, exx
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    c = synth.CONFIGS[2]
+    seed = synth.SEED_BASE + 2 + 1000 * rank       # independent cell per rank (weak scaling)
+    ws = synth.water_cell(c["lattice"], c["n"], c["n_mol"], seed)
+    ctx = exx.Context(local_rank)
+    p = exx.make_params(r_pair=c["r_pair"], r_pe=c["r_pe"], r_me=c["r_me"], tol=c["tol"], precision=exx.MIXED)
+    cr = driver.prepare(ctx, ws, p, device=local_rank)
+    info = cr.plan.info()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx.set_timing(True)
+    for _ in range(args.warmup):
+        out = driver.run(ctx, cr, pair_outputs=False, stream=sh)
+    torch.cuda.synchronize()
+
+    gpu_id = None
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        gpu_id = cvd.split(",")[local_rank].strip()
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solve_ms, n_pairs, tot_iter, tot_ref = [], 0, 0, 0
+    for _ in range(args.steps):
+        out = driver.run(ctx, cr, pair_outputs=False, stream=sh)
+        t = ctx.timing()
+        solve_ms.append(t["solve_ms"])
+        n_pairs = out["n_pairs"]
+        tot_iter = out["total_cg_iter"]
+        tot_ref = out["total_refine"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_step = elapsed / args.steps
+    value = world * n_pairs * args.steps / (elapsed / 1e3)
+
+    # roofline of the dominant kernel (the persistent pair solver)
+    s_bytes = 4.0
+    bytes_launch = algorithmic_bytes(n_pairs, tot_iter, tot_ref, info["n_pe_pair"], info["n_me_pair"], s_bytes)
+    avg_solve = sum(solve_ms) / len(solve_ms)
+    achieved = bytes_launch / (avg_solve / 1e3) / 1e9
+    peak, peak_kind = measured_hbm()
+    traffic = profile_traffic(kernel_sha())
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        phi_h = torch.empty(ws.phi.shape, dtype=torch.float64, pin_memory=True).numpy()
+        phi_h[...] = ws.phi
+        cen_h = torch.empty(ws.centres.shape, dtype=torch.float64, pin_memory=True).numpy()
+        cen_h[...] = ws.centres
+        lo_h = torch.empty(ws.box_lo.shape, dtype=torch.int32, pin_memory=True).numpy()
+        lo_h[...] = ws.box_lo
+        dxx_h = torch.empty((ws.n_orb,) + tuple(int(x) for x in cr.dbox), dtype=torch.float64,
+                            pin_memory=True).numpy()
+        dlo_h = torch.empty(cr.dbox_lo_np.shape, dtype=torch.int32, pin_memory=True).numpy()
+        dlo_h[...] = cr.dbox_lo_np
+        orb = exx.make_orbitals(ws.n_orb, ws.box, cen_h, lo_h, phi_h, exx.MEM_HOST)
+        res = exx.make_result(dxx_h, cr.dbox, dlo_h, exx.MEM_HOST)
+        exx.solve(ctx, cr.plan, ws.lattice, ws.n, orb, res, stream=sh)     # warm (allocates staging)
+        n_e2e = max(2, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            exx.solve(ctx, cr.plan, ws.lattice, ws.n, orb, res, stream=sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et = e0.elapsed_time(e1) / n_e2e
+        h2d = phi_h.nbytes + cen_h.nbytes + lo_h.nbytes + dlo_h.nbytes
+        d2h = dxx_h.nbytes + 19 * 8
+        e2e = {"value": world * res.n_pairs / (et / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": et}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(ws, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed-f32-f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": n_pairs, "n_pe": info["n_pe_pair"],
+                       "n_me": info["n_me_pair"], "n_stcl": info["n_stcl"],
+                       "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_fp64_residuals": tot_ref / max(n_pairs, 1),
+                       "ctas": info["ctas"], "threads": info["threads"],
+                       "l2": "inputs larger than L2 (orbital boxes 512 MB, D_xx 3.5 GB per step)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair_solve<float>",
+                         "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_solve,
+                         "peak_kind": f"{peak_kind} HBM copy bandwidth"},
+            "clocks": clocks,
+            "gpu_launches": 5 * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=48)
+    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * exx.h -- C ABI of the GB300 exact-exchange (EXX) pair path.
+ *
+ * The library evaluates, on one GPU, the linear-scaling exact-exchange
+ * quantities of Ko, Santra & DiStasio (arXiv 2011.07209) for a set of
+ * localized orbitals phi_i (maximally localized Wannier functions) in a
+ * general, possibly fluctuating, simulation cell:
+ *
+ *   E_xx      = - sum_<ij> w_ij  int_PE rho_ij v_ij                 (Eq. exxGen_mlwf)
+ *   D_xx^i    =   sum_j v_ij phi_j                                  (Eq. Dxx)
+ *   sigma^{a alpha} = dE_xx/dh_{a alpha}
+ *             = -2 sum_<ij> w_ij sum_b (h^-1)_{alpha b} int_PE r_b rho_ij d_a v_ij   (Eq. sxx_working)
+ *   Pi_ab     = -(1/V) sum_alpha sigma^{a alpha} h_{b alpha}        (Eq. pixx_working)
+ *
+ * over the unique pairs <ij> (i <= j, w_ii = 1, w_ij = 2) whose centres are
+ * within R_pair (Sec. III A, Step II).  For each pair the library forms
+ * rho_ij = phi_i phi_j on the Poisson subdomain of radius R_PE around the
+ * grid-resolved pair centre (Step III), takes its multipole moments up to
+ * l_max (Eq. mepole), sets the far field on the shell R_PE < r <= R_ME
+ * (Eq. me), and solves Poisson's equation (Eq. pe) by conjugate gradients with
+ * the Natan-Kronik finite-difference Laplacian of Eq. lapG_mod_nk3d, whose
+ * auxiliary directions come from the 2D bisector rule (Eqs. nk2d_aux,
+ * kappa_def) or Algorithm 1 (Step IV).  Every step runs in CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Units: Hartree atomic units (bohr, Ha).  E_xx is not scaled by the hybrid
+ * mixing fraction a_x (Eq. hyb); D_xx carries no spin or occupation factor.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Cell: lattice[alpha][a] = (L_alpha)_a (rows are lattice vectors); the
+ *    cell tensor of the paper is h = lattice^T (Sec. II B 1).  The cell must be
+ *    right-handed (det h > 0).  Grid point g sits at r = h (g / n).
+ *  - Orbital boxes: orbital i is stored on a box of box[0] x box[1] x box[2]
+ *    grid points, C order, whose element (u0,u1,u2) is the grid point
+ *    (box_lo[i] + u) mod n; the orbital is zero outside its box.  box[a] <= n[a].
+ *  - D boxes: D_xx^i is written on a box of dbox[] points starting at
+ *    dbox_lo[i], same layout.  A non-zero contribution that falls outside the
+ *    D box is an error (EXX_ERR_BOX); exx_dbox_halfwidth() gives a size that
+ *    always suffices.
+ *  - Memory: pointers are device pointers unless the structure's mem field is
+ *    EXX_MEM_HOST, in which case the library copies them through its own
+ *    device workspace (host memory should be pinned for speed).  The caller
+ *    owns every input and output buffer; the library owns its workspace.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  The
+ *    solve entry points enqueue all work on it and return after it finishes,
+ *    with the scalar results in host memory.
+ *  - Errors: every entry point returns an exx_status; EXX_OK is 0.
+ *    exx_error_string() gives a static message.  A failed call leaves the
+ *    context usable.
+ *  - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef EXX_H
+#define EXX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXX_OK = 0,
+    EXX_ERR_ARG = 1,                 /* bad argument or inconsistent sizes                  */
+    EXX_ERR_CELL = 2,                /* det h <= 0: singular or left-handed cell            */
+    EXX_ERR_HALO = 3,                /* R_ME too small: a stencil neighbour of a PE point   */
+                                     /* lies outside PE u shell                              */
+    EXX_ERR_NK = 4,                  /* no negative-definite Natan-Kronik stencil found     */
+    EXX_ERR_CG_NOT_CONVERGED = 5,    /* a pair hit cg_max_iter; see exx_result.failed_pair  */
+    EXX_ERR_CAPACITY = 6,            /* more orbitals/pairs than the plan was sized for     */
+    EXX_ERR_BOX = 7,                 /* non-zero D contribution outside a D box             */
+    EXX_ERR_OOM = 8,                 /* device or pinned allocation failed                  */
+    EXX_ERR_CUDA = 9                 /* a CUDA runtime call failed                          */
+} exx_status;
+
+enum { EXX_FP64 = 0, EXX_MIXED = 1 };          /* exx_params.precision */
+enum { EXX_MEM_DEVICE = 0, EXX_MEM_HOST = 1 };  /* memory kind of caller buffers */
+
+typedef struct exx_ctx exx_ctx;
+typedef struct exx_plan exx_plan;
+
+typedef struct {
+    double lattice[3][3];   /* rows = lattice vectors L_alpha, Cartesian bohr */
+    int n[3];               /* grid points along L_alpha, each >= 1 */
+} exx_cell;
+
+typedef struct {
+    double r_pair;          /* pair cutoff on |C_i - C_j| (minimum image), bohr (Sec. III A) */
+    double r_pe_self;       /* Poisson-subdomain radius for i == j pairs */
+    double r_pe_pair;       /* Poisson-subdomain radius for i != j pairs */
+    double r_me_self;       /* outer radius of the multipole shell, i == j */
+    double r_me_pair;       /* outer radius of the multipole shell, i != j */
+    double cg_tol;          /* stop when |b - A v|_2 <= cg_tol |b|_2 (true residual) */
+    int fd_order;           /* stencil half-width n of Eq. d2_1, 1..6 (paper default 3) */
+    int lmax;               /* multipole order, 0..6 */
+    int cg_max_iter;        /* cap on CG iterations per pair (summed over refinements) */
+    int nq;                 /* NK candidate count N_q of Algorithm 1 (paper default 15) */
+    int precision;          /* EXX_FP64: every step in FP64.  EXX_MIXED: FP32 stencil and */
+                            /* axpy inside an FP64-residual refinement loop; dot products */
+                            /* exact-product double-float; moments, E, sigma, D in FP64   */
+    int frozen;             /* 1: subdomain offsets and NK aux directions stay those of the */
+                            /* plan's cell while h changes (fixed number of points,         */
+                            /* Sec. III B 2); 0: rebuilt whenever the cell changes          */
+} exx_params;
+
+typedef struct {
+    int n_orb;              /* number of orbitals */
+    int box[3];             /* orbital box extent */
+    const double *centres;  /* [n_orb][3] Cartesian centres C_i, bohr */
+    const int *box_lo;      /* [n_orb][3] first grid index of each box */
+    const double *phi;      /* [n_orb][box0][box1][box2] orbital values */
+    int mem;                /* EXX_MEM_DEVICE or EXX_MEM_HOST for the three arrays */
+} exx_orbitals;
+
+typedef struct {
+    /* ---- inputs describing the caller's output buffers ---- */
+    double *dxx;            /* [n_orb][dbox0][dbox1][dbox2] D_xx (zeroed by the call), or NULL */
+    const int *dbox_lo;     /* [n_orb][3] first grid index of each D box (required with dxx) */
+    int dbox[3];            /* D box extent */
+    int mem;                /* EXX_MEM_DEVICE or EXX_MEM_HOST for dxx, dbox_lo and pair arrays */
+    int pair_cap;           /* capacity of the optional per-pair arrays below */
+    double *pair_e;         /* [pair_cap] int_PE rho v per pair, or NULL */
+    double *pair_sig;       /* [pair_cap][3][3] sum_b hinv_{alpha b} int r_b rho d_a v, [a][alpha], or NULL */
+    int *pair_iter;         /* [pair_cap] CG iterations per pair, or NULL */
+    /* ---- scalar outputs (host) ---- */
+    double e_xx;            /* Ha */
+    double dedh[3][3];      /* sigma^{a alpha} = dE_xx / dh_{a alpha}, Ha/bohr */
+    double stress[3][3];    /* Pi_xx^pot, Ha/bohr^3 */
+    int n_pairs;            /* unique pairs found */
+    int n_aux;              /* NK auxiliary directions used (0, 1 or 3) */
+    int n_stcl;             /* stencil points 2 n (3 + n_aux) + 1 */
+    int max_cg_iter;        /* largest per-pair CG iteration count */
+    long long total_cg_iter;/* CG iterations summed over pairs */
+    int max_refine;         /* largest number of FP64 residual evaluations of a pair */
+    int failed_pair;        /* index of the first failed pair, or -1 */
+    long long total_refine; /* FP64 residual evaluations summed over pairs */
+} exx_result;
+
+typedef struct {
+    int n_pe_self, n_me_self, n_pe_pair, n_me_pair;   /* subdomain sizes N_PE, N_ME */
+    int n_halo_self, n_halo_pair;                     /* shell points the stencil reaches */
+    int n_aux, n_stcl;
+    int dirs[6][3];         /* integer grid step of each pure-derivative direction */
+    double coef[6];         /* coefficient of sum_q w_q f(g + q d) per direction, 1/bohr^2 */
+    int aux_frozen[3][3];   /* aux directions held when params.frozen = 1 */
+    int box_self[3], box_pair[3];    /* dense CG boxes (PE plus stencil margin) */
+    long long workspace_bytes;
+    int pair_capacity;      /* largest number of pairs a solve can hold */
+    int ctas;               /* persistent CTAs of the pair kernel */
+    int threads;            /* threads per CTA */
+} exx_plan_info;
+
+/* Create a context on CUDA device `device` (made current for the call). */
+int exx_ctx_create(exx_ctx **ctx, int device);
+void exx_ctx_destroy(exx_ctx *ctx);
+
+/* Build a plan for one cell (Sec. III B-C): cell metric (Eqs. jacb, lapG_), NK
+ * stencil (Eqs. nk2d_aux .. lapG_mod_nk3d, Algorithm 1) and its definiteness
+ * check, proto-subdomain offset sets PE and shell for self and non-self pairs
+ * (Eqs. rbar, g0), the halo check, and device workspace for up to max_orb
+ * orbitals of extent box[].  Returns EXX_ERR_CELL, EXX_ERR_NK, EXX_ERR_HALO,
+ * EXX_ERR_ARG or EXX_ERR_OOM on failure (and *plan = NULL). */
+int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params,
+                    int max_orb, const int box[3], exx_plan **plan);
+void exx_plan_destroy(exx_plan *plan);
+int exx_plan_query(const exx_plan *plan, exx_plan_info *info);
+
+/* Evaluate E_xx, D_xx and sigma_xx / Pi_xx for one cell (Steps II-V).
+ * `cell` may differ from the plan's cell: with params.frozen = 1 the plan's
+ * offsets and aux directions are kept and every metric quantity follows the
+ * new cell (Sec. III B 2); otherwise the plan is rebuilt for it.  On
+ * EXX_ERR_CG_NOT_CONVERGED the other outputs are still written. */
+int exx_pairs_solve(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const exx_orbitals *orb,
+                    exx_result *res, void *stream);
+
+/* Evaluate n_cells independent cells in one persistent launch: the pairs of
+ * all cells share one work queue ordered by estimated cost.  plans[c],
+ * cells[c], orbs[c], res[c] describe cell c; the plans must come from the
+ * same context and use the same precision.  Returns the first non-OK status
+ * over the cells. */
+int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, const exx_cell *cells,
+                          const exx_orbitals *orbs, exx_result *res, void *stream);
+
+/* Copy the unique pair list of the plan's last solve to host memory: rows of
+ * (i, j, k0, k1, k2, g0, g1, g2) with i <= j in lexicographic order, k the
+ * lattice image of j nearest to i and g the grid-resolved pair centre
+ * (Sec. III A Step II, Eq. l2g).  *n receives the pair count; fails with
+ * EXX_ERR_CAPACITY if it exceeds cap. */
+int exx_get_pair_list(exx_plan *plan, int cap, int *n, int *rows);
+
+/* Index half-widths of a D box that holds every contribution of the pairs of
+ * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
+int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);
+
+/* Stage timing of the context's last solve, measured with CUDA events
+ * recorded on the solve's stream while enabled: ms[0] solid-harmonic tables
+ * (only when the cell changed), ms[1] pair list, ms[2] persistent pair
+ * solver, ms[3] per-cell reductions.  Disabled by default. */
+int exx_ctx_set_timing(exx_ctx *ctx, int enable);
+int exx_ctx_get_timing(const exx_ctx *ctx, double ms[4]);
+
+const char *exx_error_string(int code);
+
+/* Library version string. */
+const char *exx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXX_H */

@@ -1,0 +1,770 @@
+// api.cu -- the C ABI of include/exx.h: contexts, plans, workspace and the
+// launch sequence of one EXX evaluation (pair list -> persistent pair solver
+// -> ordered per-cell reductions), for one cell or a batch of cells.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/exx.h"
+#include "exx_dev.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace exx;
+
+#define CK(call)                                     \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return EXX_ERR_CUDA;  \
+    } while (0)
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class T>
+int dev_alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return EXX_OK;
+    if (cudaMalloc((void **)p, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return EXX_ERR_OOM;
+    }
+    return EXX_OK;
+}
+
+template <class T>
+void dev_free(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+struct exx_ctx {
+    int device = 0;
+    int n_sm = 0;
+    // persistent solver slots (shared by every plan of the context)
+    char *slots = nullptr;
+    size_t slots_bytes = 0;
+    SolveSlots sl_mixed{}, sl_fp64{};
+    size_t box_max = 0, npe_max = 0;
+    bool slots_dirty = false;
+    // pair list
+    ListDev list{};
+    int rows_cap = 0;
+    // cells and results
+    CellDev *d_cells = nullptr;
+    CellResult *d_res = nullptr;
+    CellDev *h_cells = nullptr;       // pinned
+    CellResult *h_res = nullptr;      // pinned
+    int cells_cap = 0;
+    int inner_shift = 14;
+    bool timing = false;
+    cudaEvent_t ev[5] = {};
+    double ms[4] = {};
+};
+
+struct exx_plan {
+    exx_ctx *ctx = nullptr;
+    exx_cell cell0{};      // cell the offsets / aux directions were built for
+    exx_cell cell{};       // cell of the last metric update
+    exx_params params{};
+    Metric metric{};
+    Stencil stencil{};
+    int aux[3][3] = {};
+    int n_aux = 0;
+    OffsetSet off[2];
+    SetLayout lay[2];
+    int32_t *d_pe_m[2] = {}, *d_pe_off[2] = {}, *d_sh_m[2] = {}, *d_halo_off[2] = {};
+    double *d_S64[2] = {}, *d_T64[2] = {};
+    float *d_S32[2] = {}, *d_T32[2] = {};
+    bool tables_valid = false;
+    // device copies for host-memory inputs
+    int max_orb = 0;
+    int box[3] = {};
+    double *d_phi = nullptr, *d_centres = nullptr;
+    int32_t *d_box_lo = nullptr;
+    double *d_dxx = nullptr;
+    size_t dxx_cap = 0;
+    int32_t *d_dbox_lo = nullptr;
+    double *d_pair_e = nullptr;   // per-pair staging for host-memory outputs
+    PairRec *d_pairs = nullptr;   // pair list of the last solve
+    int pairs_cap = 0;
+    int last_count = 0;
+    PairOut *d_out = nullptr;
+};
+
+static bool same_cell(const exx_cell &a, const exx_cell &b)
+{
+    return std::memcmp(a.lattice, b.lattice, sizeof(a.lattice)) == 0 && a.n[0] == b.n[0] && a.n[1] == b.n[1] &&
+           a.n[2] == b.n[2];
+}
+
+static int check_params(const exx_params *p)
+{
+    if (!p) return EXX_ERR_ARG;
+    if (p->fd_order < 1 || p->fd_order > kMaxFd) return EXX_ERR_ARG;
+    if (p->lmax < 0 || p->lmax > kMaxL) return EXX_ERR_ARG;
+    if (!(p->r_pair >= 0.0) || !(p->cg_tol > 0.0) || p->cg_max_iter < 1 || p->nq < 1) return EXX_ERR_ARG;
+    if (p->precision != EXX_FP64 && p->precision != EXX_MIXED) return EXX_ERR_ARG;
+    return EXX_OK;
+}
+
+static void free_geometry(exx_plan *p)
+{
+    for (int s = 0; s < 2; ++s) {
+        dev_free(p->d_pe_m[s]);
+        dev_free(p->d_pe_off[s]);
+        dev_free(p->d_sh_m[s]);
+        dev_free(p->d_halo_off[s]);
+        dev_free(p->d_S64[s]);
+        dev_free(p->d_T64[s]);
+        dev_free(p->d_S32[s]);
+        dev_free(p->d_T32[s]);
+    }
+    p->tables_valid = false;
+}
+
+// Offsets, stencil and layout for cell0 (and the aux directions to freeze).
+static int build_geometry(exx_plan *p)
+{
+    int e = make_metric(p->cell0.lattice, p->cell0.n, p->metric);
+    if (e) return e;
+    e = make_stencil(p->metric, p->params.fd_order, p->params.nq, nullptr, 0, p->stencil);
+    if (e) return e;
+    p->n_aux = p->stencil.n_aux;
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) p->aux[a][k] = a < p->n_aux ? p->stencil.dir[3 + a][k] : 0;
+    const double rpe[2] = {p->params.r_pe_self, p->params.r_pe_pair};
+    const double rme[2] = {p->params.r_me_self, p->params.r_me_pair};
+    free_geometry(p);
+    for (int s = 0; s < 2; ++s) {
+        e = make_offsets(p->metric, rpe[s], rme[s], p->off[s]);
+        if (e) return e;
+        e = make_layout(p->off[s], p->stencil, p->params.fd_order, p->lay[s]);
+        if (e) return e;
+        const SetLayout &L = p->lay[s];
+        if ((e = dev_alloc(&p->d_pe_m[s], L.n_pe)) || (e = dev_alloc(&p->d_pe_off[s], L.n_pe)) ||
+            (e = dev_alloc(&p->d_sh_m[s], L.n_shell)) || (e = dev_alloc(&p->d_halo_off[s], L.n_halo)) ||
+            (e = dev_alloc(&p->d_S64[s], (size_t)L.n_pe * kNlm)) ||
+            (e = dev_alloc(&p->d_S32[s], (size_t)L.n_pe * kNlm)) ||
+            (e = dev_alloc(&p->d_T64[s], (size_t)L.n_shell * kNlm)) ||
+            (e = dev_alloc(&p->d_T32[s], (size_t)L.n_shell * kNlm)))
+            return e;
+        CK(cudaMemcpy(p->d_pe_m[s], L.pe_m.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->d_pe_off[s], L.pe_off.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
+        if (L.n_shell) CK(cudaMemcpy(p->d_sh_m[s], L.sh_m.data(), 4 * L.n_shell, cudaMemcpyHostToDevice));
+        if (L.n_halo) CK(cudaMemcpy(p->d_halo_off[s], L.halo_off.data(), 4 * L.n_halo, cudaMemcpyHostToDevice));
+    }
+    p->cell = p->cell0;
+    p->tables_valid = false;
+    return EXX_OK;
+}
+
+// Metric and stencil coefficients for the current cell, offsets held fixed.
+static int update_metric(exx_plan *p, const exx_cell &cell)
+{
+    Metric m;
+    int e = make_metric(cell.lattice, cell.n, m);
+    if (e) return e;
+    Stencil st;
+    e = make_stencil(m, p->params.fd_order, p->params.nq, p->n_aux ? p->aux : nullptr, p->n_aux, st);
+    if (e) return e;
+    // the frozen directions keep the layout; re-check the halo for safety
+    for (int s = 0; s < 2; ++s) {
+        SetLayout L;
+        e = make_layout(p->off[s], st, p->params.fd_order, L);
+        if (e) return e;
+    }
+    p->metric = m;
+    p->stencil = st;
+    p->cell = cell;
+    p->tables_valid = false;
+    return EXX_OK;
+}
+
+static void fill_celldev(const exx_plan *p, CellDev &C)
+{
+    std::memset(&C, 0, sizeof(C));
+    const Metric &m = p->metric;
+    std::memcpy(C.h, m.h, sizeof(C.h));
+    std::memcpy(C.hinv, m.hinv, sizeof(C.hinv));
+    std::memcpy(C.J, m.J, sizeof(C.J));
+    C.vol = m.vol;
+    C.dv = m.dv;
+    for (int a = 0; a < 3; ++a) {
+        C.dxi[a] = m.dxi[a];
+        C.n[a] = m.n[a];
+    }
+    const Stencil &st = p->stencil;
+    const int n = p->params.fd_order;
+    C.ndir = st.ndir;
+    C.fd_n = n;
+    C.lmax = p->params.lmax;
+    C.nlm = (C.lmax + 1) * (C.lmax + 1);
+    double w2[kMaxFd + 1], w1[kMaxFd + 1];
+    fd_weights(n, w2, w1);
+    for (int d = 0; d < st.ndir; ++d) {
+        for (int k = 0; k < 3; ++k) C.dir[d][k] = st.dir[d][k];
+        for (int s = 0; s <= n; ++s) {
+            C.cw64[d][s] = st.coef[d] * w2[s];
+            C.cw32[d][s] = (float)C.cw64[d][s];
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s <= n; ++s) C.w1dx[a][s] = w1[s] / m.dxi[a];
+    C.tol = p->params.cg_tol;
+    C.max_iter = p->params.cg_max_iter;
+    C.precision = p->params.precision;
+    C.r_pair2 = p->params.r_pair * p->params.r_pair;
+    for (int s = 0; s < 2; ++s) {
+        const SetLayout &L = p->lay[s];
+        SetDev &S = C.set[s];
+        S.n_pe = L.n_pe;
+        S.n_shell = L.n_shell;
+        S.n_halo = L.n_halo;
+        for (int a = 0; a < 3; ++a) {
+            S.B[a] = L.B[a];
+            S.c[a] = L.c[a];
+            S.gstride[a] = L.gstride[a];
+        }
+        S.box = L.box;
+        for (int d = 0; d < 6; ++d) S.dstride[d] = L.dstride[d];
+        S.pe_m = p->d_pe_m[s];
+        S.pe_off = p->d_pe_off[s];
+        S.sh_m = p->d_sh_m[s];
+        S.halo_off = p->d_halo_off[s];
+        S.S64 = p->d_S64[s];
+        S.S32 = p->d_S32[s];
+        S.T64 = p->d_T64[s];
+        S.T32 = p->d_T32[s];
+    }
+}
+
+static int ensure_cells(exx_ctx *c, int n)
+{
+    if (n <= c->cells_cap) return EXX_OK;
+    dev_free(c->d_cells);
+    dev_free(c->d_res);
+    if (c->h_cells) cudaFreeHost(c->h_cells);
+    if (c->h_res) cudaFreeHost(c->h_res);
+    c->h_cells = nullptr;
+    c->h_res = nullptr;
+    c->cells_cap = 0;
+    int e;
+    if ((e = dev_alloc(&c->d_cells, n)) || (e = dev_alloc(&c->d_res, n))) return e;
+    if (cudaMallocHost((void **)&c->h_cells, sizeof(CellDev) * n) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_res, sizeof(CellResult) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return EXX_ERR_OOM;
+    }
+    c->cells_cap = n;
+    return EXX_OK;
+}
+
+static int ensure_list(exx_ctx *c, int rows, long long pairs)
+{
+    ListDev &L = c->list;
+    if (rows <= c->rows_cap && pairs <= L.capacity && L.total) return EXX_OK;
+    if (pairs > (1LL << 30)) return EXX_ERR_CAPACITY;
+    dev_free(L.row_count);
+    dev_free(L.row_start);
+    dev_free(L.cell_start);
+    dev_free(L.cell_count);
+    dev_free(L.total);
+    dev_free(L.pairs);
+    dev_free(L.out);
+    const int rcap = std::max(rows, 1);
+    const int pcap = (int)std::max(pairs, 1LL);
+    int e;
+    if ((e = dev_alloc(&L.row_count, rcap)) || (e = dev_alloc(&L.row_start, rcap)) ||
+        (e = dev_alloc(&L.cell_start, 64)) || (e = dev_alloc(&L.cell_count, 64)) || (e = dev_alloc(&L.total, 4)) ||
+        (e = dev_alloc(&L.pairs, pcap)) || (e = dev_alloc(&L.out, pcap)))
+        return e;
+    L.queue = L.total + 1;
+    L.overflow = L.total + 2;
+    L.capacity = pcap;
+    c->rows_cap = rcap;
+    return EXX_OK;
+}
+
+static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
+{
+    box_max = std::max(box_max, c->box_max);
+    npe_max = std::max(npe_max, c->npe_max);
+    const int bpm = std::max(1, solve_blocks_per_sm(mixed));
+    const int n_slots = bpm * c->n_sm;
+    // one layout that serves both precisions: boxes and vectors sized for doubles
+    SolveSlots s{};
+    size_t o = 0;
+    s.off_vbox = o;
+    o += align256(8 * box_max);
+    s.off_pbox = o;
+    o += align256(8 * box_max);
+    s.off_rho = o;
+    o += align256(8 * npe_max);
+    s.off_r64 = o;
+    o += align256(8 * npe_max);
+    s.off_r = o;
+    o += align256(8 * npe_max);
+    s.off_q = o;
+    o += align256(8 * npe_max);
+    s.off_e = o;
+    o += align256(8 * npe_max);
+    s.slot_bytes = o;
+    s.n_slots = n_slots;
+    const size_t need = s.slot_bytes * (size_t)n_slots;
+    if (need > c->slots_bytes || box_max > c->box_max || npe_max > c->npe_max) {
+        if (c->slots) cudaFree(c->slots);
+        c->slots = nullptr;
+        c->slots_bytes = 0;
+        if (cudaMalloc((void **)&c->slots, need) != cudaSuccess) {
+            cudaGetLastError();
+            return EXX_ERR_OOM;
+        }
+        c->slots_bytes = need;
+        c->box_max = box_max;
+        c->npe_max = npe_max;
+        c->slots_dirty = true;
+    }
+    if (c->slots_dirty) {
+        CK(cudaMemset(c->slots, 0, c->slots_bytes));
+        c->slots_dirty = false;
+    }
+    s.base = c->slots;
+    // the slot count may differ per precision; the memory holds the larger
+    const size_t fit = c->slots_bytes / s.slot_bytes;
+    s.n_slots = (int)std::min<size_t>((size_t)n_slots, fit);
+    (mixed ? c->sl_mixed : c->sl_fp64) = s;
+    return EXX_OK;
+}
+
+extern "C" {
+
+const char *exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
+
+const char *exx_error_string(int code)
+{
+    switch (code) {
+    case EXX_OK: return "ok";
+    case EXX_ERR_ARG: return "invalid argument";
+    case EXX_ERR_CELL: return "cell tensor is singular or left-handed (det h <= 0)";
+    case EXX_ERR_HALO: return "R_ME too small: a stencil neighbour of a Poisson point lies outside the ME sphere";
+    case EXX_ERR_NK: return "no negative-definite Natan-Kronik stencil for this cell";
+    case EXX_ERR_CG_NOT_CONVERGED: return "conjugate gradients reached cg_max_iter for a pair";
+    case EXX_ERR_CAPACITY: return "more orbitals or pairs than the plan or context can hold";
+    case EXX_ERR_BOX: return "a non-zero D_xx contribution falls outside its D box";
+    case EXX_ERR_OOM: return "out of device or pinned host memory";
+    case EXX_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown error";
+    }
+}
+
+int exx_ctx_create(exx_ctx **ctx, int device)
+{
+    if (!ctx) return EXX_ERR_ARG;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return EXX_ERR_CUDA;
+    }
+    CK(cudaSetDevice(device));
+    exx_ctx *c = new (std::nothrow) exx_ctx();
+    if (!c) return EXX_ERR_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (const char *s = std::getenv("EXX_INNER_SHIFT")) c->inner_shift = std::max(4, std::min(22, std::atoi(s)));
+    *ctx = c;
+    return EXX_OK;
+}
+
+int exx_ctx_set_timing(exx_ctx *c, int enable)
+{
+    if (!c) return EXX_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (enable && !c->ev[0])
+        for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&c->ev[k]));
+    c->timing = enable != 0;
+    return EXX_OK;
+}
+
+int exx_ctx_get_timing(const exx_ctx *c, double ms[4])
+{
+    if (!c || !ms) return EXX_ERR_ARG;
+    for (int k = 0; k < 4; ++k) ms[k] = c->ms[k];
+    return EXX_OK;
+}
+
+void exx_ctx_destroy(exx_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (int k = 0; k < 5; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->slots) cudaFree(c->slots);
+    ListDev &L = c->list;
+    dev_free(L.row_count);
+    dev_free(L.row_start);
+    dev_free(L.cell_start);
+    dev_free(L.cell_count);
+    dev_free(L.total);
+    dev_free(L.pairs);
+    dev_free(L.out);
+    dev_free(c->d_cells);
+    dev_free(c->d_res);
+    if (c->h_cells) cudaFreeHost(c->h_cells);
+    if (c->h_res) cudaFreeHost(c->h_res);
+    delete c;
+}
+
+int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params, int max_orb, const int box[3],
+                    exx_plan **plan)
+{
+    if (!plan) return EXX_ERR_ARG;
+    *plan = nullptr;
+    if (!ctx || !cell || !box || max_orb < 0) return EXX_ERR_ARG;
+    int e = check_params(params);
+    if (e) return e;
+    for (int a = 0; a < 3; ++a)
+        if (cell->n[a] < 1 || box[a] < 1 || box[a] > cell->n[a]) return EXX_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    exx_plan *p = new (std::nothrow) exx_plan();
+    if (!p) return EXX_ERR_OOM;
+    p->ctx = ctx;
+    p->cell0 = *cell;
+    p->params = *params;
+    p->max_orb = max_orb;
+    for (int a = 0; a < 3; ++a) p->box[a] = box[a];
+    e = build_geometry(p);
+    if (!e) {
+        const long long pairs = (long long)max_orb * (max_orb + 1) / 2;
+        p->pairs_cap = (int)std::min<long long>(pairs, 1LL << 30);
+        if ((e = dev_alloc(&p->d_pairs, std::max(p->pairs_cap, 1))) ||
+            (e = dev_alloc(&p->d_out, std::max(p->pairs_cap, 1))))
+            ;
+    }
+    if (e) {
+        exx_plan_destroy(p);
+        return e;
+    }
+    *plan = p;
+    return EXX_OK;
+}
+
+void exx_plan_destroy(exx_plan *p)
+{
+    if (!p) return;
+    cudaSetDevice(p->ctx->device);
+    free_geometry(p);
+    dev_free(p->d_phi);
+    dev_free(p->d_centres);
+    dev_free(p->d_box_lo);
+    dev_free(p->d_dxx);
+    dev_free(p->d_dbox_lo);
+    dev_free(p->d_pairs);
+    dev_free(p->d_out);
+    delete p;
+}
+
+int exx_plan_query(const exx_plan *p, exx_plan_info *info)
+{
+    if (!p || !info) return EXX_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_pe_self = p->lay[0].n_pe;
+    info->n_me_self = p->lay[0].n_pe + p->lay[0].n_shell;
+    info->n_pe_pair = p->lay[1].n_pe;
+    info->n_me_pair = p->lay[1].n_pe + p->lay[1].n_shell;
+    info->n_halo_self = p->lay[0].n_halo;
+    info->n_halo_pair = p->lay[1].n_halo;
+    info->n_aux = p->stencil.n_aux;
+    info->n_stcl = 2 * p->params.fd_order * p->stencil.ndir + 1;
+    for (int d = 0; d < 6; ++d) {
+        for (int k = 0; k < 3; ++k) info->dirs[d][k] = d < p->stencil.ndir ? p->stencil.dir[d][k] : 0;
+        info->coef[d] = d < p->stencil.ndir ? p->stencil.coef[d] : 0.0;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) info->aux_frozen[a][k] = p->aux[a][k];
+    for (int a = 0; a < 3; ++a) {
+        info->box_self[a] = p->lay[0].B[a];
+        info->box_pair[a] = p->lay[1].B[a];
+    }
+    const exx_ctx *c = p->ctx;
+    const SolveSlots &s = p->params.precision == EXX_MIXED ? c->sl_mixed : c->sl_fp64;
+    info->workspace_bytes = (long long)c->slots_bytes;
+    info->pair_capacity = p->pairs_cap;
+    info->ctas = s.n_slots;
+    info->threads = kSolveThreads;
+    return EXX_OK;
+}
+
+int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int hw[3])
+{
+    if (!cell || !params || !hw) return EXX_ERR_ARG;
+    Metric m;
+    int e = make_metric(cell->lattice, cell->n, m);
+    if (e) return e;
+    const double rme = std::max(params->r_me_self, params->r_me_pair);
+    for (int a = 0; a < 3; ++a) {
+        const double rn = std::sqrt(m.hinv[a][0] * m.hinv[a][0] + m.hinv[a][1] * m.hinv[a][1] + m.hinv[a][2] * m.hinv[a][2]);
+        hw[a] = (int)std::ceil((0.5 * params->r_pair + rme) * cell->n[a] * rn) + 1;
+    }
+    return EXX_OK;
+}
+
+int exx_get_pair_list(exx_plan *p, int cap, int *n, int *rows)
+{
+    if (!p || !n) return EXX_ERR_ARG;
+    *n = p->last_count;
+    if (p->last_count > cap) return EXX_ERR_CAPACITY;
+    if (p->last_count == 0) return EXX_OK;
+    if (!rows) return EXX_ERR_ARG;
+    std::vector<PairRec> h(p->last_count);
+    CK(cudaSetDevice(p->ctx->device));
+    CK(cudaMemcpy(h.data(), p->d_pairs, sizeof(PairRec) * p->last_count, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < p->last_count; ++t) {
+        int *r = rows + 8 * (size_t)t;
+        r[0] = h[t].i;
+        r[1] = h[t].j;
+        for (int a = 0; a < 3; ++a) {
+            r[2 + a] = h[t].k[a];
+            r[5 + a] = h[t].g[a];
+        }
+    }
+    return EXX_OK;
+}
+
+int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, const exx_cell *cells,
+                          const exx_orbitals *orbs, exx_result *res, void *stream_)
+{
+    if (!ctx || n_cells < 1 || !plans || !cells || !orbs || !res) return EXX_ERR_ARG;
+    if (n_cells > 64) return EXX_ERR_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    CK(cudaSetDevice(ctx->device));
+    const int prec = plans[0]->params.precision;
+    for (int c = 0; c < n_cells; ++c) {
+        exx_plan *p = plans[c];
+        if (!p || p->ctx != ctx || p->params.precision != prec) return EXX_ERR_ARG;
+        const exx_orbitals &o = orbs[c];
+        if (o.n_orb < 0 || o.n_orb > p->max_orb) return EXX_ERR_CAPACITY;
+        if (o.n_orb > 0 && (!o.centres || !o.box_lo || !o.phi)) return EXX_ERR_ARG;
+        for (int a = 0; a < 3; ++a)
+            if (o.box[a] != p->box[a] || cells[c].n[a] != p->cell0.n[a]) return EXX_ERR_ARG;
+        if (res[c].dxx && !res[c].dbox_lo) return EXX_ERR_ARG;
+        if (res[c].dxx)
+            for (int a = 0; a < 3; ++a)
+                if (res[c].dbox[a] < 1 || res[c].dbox[a] > cells[c].n[a]) return EXX_ERR_ARG;
+    }
+    // geometry for the current cells
+    for (int c = 0; c < n_cells; ++c) {
+        exx_plan *p = plans[c];
+        if (same_cell(cells[c], p->cell)) continue;
+        int e;
+        if (p->params.frozen) {
+            e = update_metric(p, cells[c]);
+        } else {
+            p->cell0 = cells[c];
+            e = build_geometry(p);
+        }
+        if (e) return e;
+    }
+    // cells queued by decreasing per-pair cost (largest Poisson subdomain first)
+    std::vector<int> order(n_cells);
+    for (int c = 0; c < n_cells; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return plans[a]->lay[1].n_pe > plans[b]->lay[1].n_pe;
+    });
+    int e = ensure_cells(ctx, n_cells);
+    if (e) return e;
+    int rows = 0;
+    long long pairs = 0;
+    size_t box_max = 0, npe_max = 0;
+    for (int c = 0; c < n_cells; ++c) {
+        rows += orbs[c].n_orb;
+        pairs += (long long)orbs[c].n_orb * (orbs[c].n_orb + 1) / 2;
+        for (int s = 0; s < 2; ++s) {
+            box_max = std::max(box_max, (size_t)plans[c]->lay[s].box);
+            npe_max = std::max(npe_max, (size_t)plans[c]->lay[s].n_pe);
+        }
+    }
+    if ((e = ensure_list(ctx, rows, pairs))) return e;
+    if ((e = ensure_slots(ctx, box_max, npe_max, prec == EXX_MIXED))) return e;
+
+    // stage inputs and fill the per-cell constants (queue order)
+    int row_base = 0;
+    for (int qi = 0; qi < n_cells; ++qi) {
+        const int c = order[qi];
+        exx_plan *p = plans[c];
+        const exx_orbitals &o = orbs[c];
+        exx_result &r = res[c];
+        CellDev &C = ctx->h_cells[qi];
+        fill_celldev(p, C);
+        C.n_orb = o.n_orb;
+        for (int a = 0; a < 3; ++a) C.box[a] = o.box[a];
+        C.row_base = row_base;
+        C.cell_index = c;
+        row_base += o.n_orb;
+        const size_t bsz = (size_t)o.box[0] * o.box[1] * o.box[2];
+        if (o.mem == EXX_MEM_HOST && o.n_orb > 0) {
+            if (!p->d_phi) {
+                if ((e = dev_alloc(&p->d_phi, bsz * p->max_orb)) || (e = dev_alloc(&p->d_centres, 3 * (size_t)p->max_orb)) ||
+                    (e = dev_alloc(&p->d_box_lo, 3 * (size_t)p->max_orb)))
+                    return e;
+            }
+            CK(cudaMemcpyAsync(p->d_phi, o.phi, 8 * bsz * o.n_orb, cudaMemcpyHostToDevice, stream));
+            CK(cudaMemcpyAsync(p->d_centres, o.centres, 24 * (size_t)o.n_orb, cudaMemcpyHostToDevice, stream));
+            CK(cudaMemcpyAsync(p->d_box_lo, o.box_lo, 12 * (size_t)o.n_orb, cudaMemcpyHostToDevice, stream));
+            C.phi = p->d_phi;
+            C.centres = p->d_centres;
+            C.box_lo = p->d_box_lo;
+        } else {
+            C.phi = o.phi;
+            C.centres = o.centres;
+            C.box_lo = o.box_lo;
+        }
+        C.dxx = nullptr;
+        if (r.dxx) {
+            const size_t dsz = (size_t)r.dbox[0] * r.dbox[1] * r.dbox[2] * o.n_orb;
+            for (int a = 0; a < 3; ++a) C.dbox[a] = r.dbox[a];
+            if (r.mem == EXX_MEM_HOST) {
+                if (p->dxx_cap < dsz) {
+                    dev_free(p->d_dxx);
+                    dev_free(p->d_dbox_lo);
+                    if ((e = dev_alloc(&p->d_dxx, dsz)) || (e = dev_alloc(&p->d_dbox_lo, 3 * (size_t)p->max_orb))) return e;
+                    p->dxx_cap = dsz;
+                }
+                CK(cudaMemcpyAsync(p->d_dbox_lo, r.dbox_lo, 12 * (size_t)o.n_orb, cudaMemcpyHostToDevice, stream));
+                C.dxx = p->d_dxx;
+                C.dbox_lo = p->d_dbox_lo;
+            } else {
+                C.dxx = r.dxx;
+                C.dbox_lo = r.dbox_lo;
+            }
+            if (dsz) CK(cudaMemsetAsync(C.dxx, 0, 8 * dsz, stream));
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->d_cells, ctx->h_cells, sizeof(CellDev) * n_cells, cudaMemcpyHostToDevice, stream));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], stream));
+    for (int qi = 0; qi < n_cells; ++qi) {
+        exx_plan *p = plans[order[qi]];
+        if (p->tables_valid) continue;
+        for (int s = 0; s < 2; ++s) {
+            const SetLayout &L = p->lay[s];
+            CK(launch_tables(ctx->d_cells + qi, s, L.n_pe + L.n_shell, p->d_S64[s], p->d_S32[s], p->d_T64[s],
+                             p->d_T32[s], stream));
+        }
+        p->tables_valid = true;
+    }
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], stream));
+    CK(launch_pair_list(ctx->d_cells, n_cells, rows, ctx->list, stream));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], stream));
+    const bool mixed = prec == EXX_MIXED;
+    CK(launch_solve(ctx->d_cells, ctx->list, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], stream));
+    CK(launch_finalize(ctx->d_cells, n_cells, ctx->list, ctx->d_res, stream));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], stream));
+    CK(cudaMemcpyAsync(ctx->h_res, ctx->d_res, sizeof(CellResult) * n_cells, cudaMemcpyDeviceToHost, stream));
+    int h_start[64], h_count[64];
+    CK(cudaMemcpyAsync(h_start, ctx->list.cell_start, 4 * n_cells, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(h_count, ctx->list.cell_count, 4 * n_cells, cudaMemcpyDeviceToHost, stream));
+    if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->slots_dirty = true;
+        return EXX_ERR_CUDA;
+    }
+    if (ctx->timing)
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]);
+            ctx->ms[k] = t;
+        }
+    int status = EXX_OK;
+    for (int qi = 0; qi < n_cells; ++qi) {
+        const int c = order[qi];
+        exx_plan *p = plans[c];
+        exx_result &r = res[c];
+        const CellResult &cr = ctx->h_res[qi];
+        const int cnt = cr.status == EXX_ERR_CAPACITY ? 0 : h_count[qi];
+        r.e_xx = cr.e_xx;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                r.dedh[a][b] = cr.dedh[3 * a + b];
+                r.stress[a][b] = cr.stress[3 * a + b];
+            }
+        r.n_pairs = cnt;
+        r.n_aux = p->stencil.n_aux;
+        r.n_stcl = 2 * p->params.fd_order * p->stencil.ndir + 1;
+        r.max_cg_iter = cr.max_iter;
+        r.total_cg_iter = cr.total_iter;
+        r.max_refine = cr.max_refine;
+        r.total_refine = cr.total_refine;
+        r.failed_pair = cr.failed_pair;
+        // keep this cell's pair list and per-pair outputs with the plan
+        p->last_count = std::min(cnt, p->pairs_cap);
+        if (p->last_count) {
+            CK(cudaMemcpyAsync(p->d_pairs, ctx->list.pairs + h_start[qi], sizeof(PairRec) * p->last_count,
+                               cudaMemcpyDeviceToDevice, stream));
+            CK(cudaMemcpyAsync(p->d_out, ctx->list.out + h_start[qi], sizeof(PairOut) * p->last_count,
+                               cudaMemcpyDeviceToDevice, stream));
+        }
+        if (r.dxx && r.mem == EXX_MEM_HOST) {
+            const size_t dsz = (size_t)r.dbox[0] * r.dbox[1] * r.dbox[2] * orbs[c].n_orb;
+            if (dsz) CK(cudaMemcpyAsync(r.dxx, p->d_dxx, 8 * dsz, cudaMemcpyDeviceToHost, stream));
+        }
+        if (cr.status && status == EXX_OK) status = cr.status;
+    }
+    // optional per-pair outputs
+    bool any_pair_out = false;
+    for (int c = 0; c < n_cells; ++c)
+        if (res[c].pair_e || res[c].pair_sig || res[c].pair_iter) any_pair_out = true;
+    if (any_pair_out) {
+        CK(cudaStreamSynchronize(stream));
+        for (int c = 0; c < n_cells; ++c) {
+            exx_plan *p = plans[c];
+            exx_result &r = res[c];
+            if (!(r.pair_e || r.pair_sig || r.pair_iter)) continue;
+            if (p->last_count > r.pair_cap) {
+                if (status == EXX_OK) status = EXX_ERR_CAPACITY;
+                continue;
+            }
+            std::vector<PairOut> h(p->last_count);
+            if (p->last_count)
+                CK(cudaMemcpy(h.data(), p->d_out, sizeof(PairOut) * p->last_count, cudaMemcpyDeviceToHost));
+            std::vector<double> e(p->last_count), sg(9 * (size_t)p->last_count);
+            std::vector<int> it(p->last_count);
+            for (int t = 0; t < p->last_count; ++t) {
+                e[t] = h[t].e;
+                for (int k = 0; k < 9; ++k) sg[9 * (size_t)t + k] = h[t].sig[k];
+                it[t] = h[t].iters;
+            }
+            const cudaMemcpyKind kind = r.mem == EXX_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+            if (r.pair_e && p->last_count) CK(cudaMemcpy(r.pair_e, e.data(), 8 * (size_t)p->last_count, kind));
+            if (r.pair_sig && p->last_count) CK(cudaMemcpy(r.pair_sig, sg.data(), 72 * (size_t)p->last_count, kind));
+            if (r.pair_iter && p->last_count) CK(cudaMemcpy(r.pair_iter, it.data(), 4 * (size_t)p->last_count, kind));
+        }
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return EXX_ERR_CUDA;
+    }
+    return status;
+}
+
+int exx_pairs_solve(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const exx_orbitals *orb, exx_result *res,
+                    void *stream)
+{
+    if (!plan) return EXX_ERR_ARG;
+    exx_plan *plans[1] = {plan};
+    return exx_pairs_solve_batch(ctx, 1, plans, cell, orb, res, stream);
+}
+
+}  // extern "C"

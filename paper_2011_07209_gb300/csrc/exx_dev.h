@@ -1,0 +1,103 @@
+// exx_dev.h -- device-visible structures of the EXX pair path (library-internal).
+#pragma once
+#include <cstdint>
+
+namespace exx {
+
+constexpr int kNlm = 49;   // (lmax + 1)^2 for lmax = 6; tables are padded to this
+
+// Geometry of one subdomain kind (self pairs or non-self pairs) of one cell.
+struct SetDev {
+    int n_pe, n_shell, n_halo;
+    int B[3], c[3];
+    long long box;                 // elements of the dense CG box
+    int dstride[6];                // box stride of each stencil direction
+    int gstride[3];                // box stride of each lattice axis
+    const int32_t *pe_m;           // [n_pe] packed offsets (lexicographic)
+    const int32_t *pe_off;         // [n_pe] dense-box offsets
+    const int32_t *sh_m;           // [n_shell] packed offsets, halo points first
+    const int32_t *halo_off;       // [n_halo] dense-box offsets
+    const double *S64;             // [n_pe][kNlm] regular solid harmonics r^l Y_lm(r-bar)
+    const float *S32;
+    const double *T64;             // [kNlm][n_shell] 4 pi / (2l+1) r^l Y_lm / r^(2l+1)
+    const float *T32;
+};
+
+// Everything a pair of one cell needs; one per cell, in device memory.
+struct CellDev {
+    double h[3][3], hinv[3][3], J[3][3];
+    double vol, dv, dxi[3];
+    int n[3];
+    int ndir, fd_n, lmax, nlm;
+    int dir[6][3];
+    double cw64[6][8];             // coef_d * w2_s, s = 0..n
+    float cw32[6][8];
+    double w1dx[3][8];             // w1_s / dxi_alpha
+    double tol;
+    int max_iter, precision;
+    double r_pair2;
+    SetDev set[2];                 // [0] self pairs, [1] non-self pairs
+    // orbitals (device copies)
+    const double *phi;
+    const int32_t *box_lo;
+    int box[3];
+    int n_orb;
+    const double *centres;
+    // D output
+    double *dxx;
+    const int32_t *dbox_lo;
+    int dbox[3];
+    // rows of the pair list of this cell: global row index base
+    int row_base;
+    int cell_index;
+};
+
+// One unique pair (i <= j): lattice image k of j and grid-resolved centre g.
+struct PairRec {
+    int i, j;
+    int k[3];
+    int g[3];
+    int cell;
+    int pad;
+};
+
+// Per-pair outputs (indexed by the global pair index).
+struct PairOut {
+    double e;          // int_PE rho v
+    double sig[9];     // [a][alpha] sum_b hinv_{alpha b} int r_b rho d_a v
+    int iters;
+    int refine;
+    int status;
+    int pad;
+};
+
+// Per-cell reduced results.
+struct CellResult {
+    double e_xx;
+    double dedh[9];
+    double stress[9];
+    long long total_iter;
+    long long total_refine;
+    int n_pairs;
+    int status;
+    int failed_pair;
+    int max_iter;
+    int max_refine;
+    int pad;
+};
+
+// Pair-list bookkeeping in device memory.
+struct ListDev {
+    int *row_count;      // [total rows]  pairs of row (cell, i)
+    int *row_start;      // [total rows]
+    int *cell_start;     // [n_cells]
+    int *cell_count;     // [n_cells]
+    int *total;          // [1]
+    int *queue;          // [1] work-queue counter
+    int *overflow;       // [1]
+    PairRec *pairs;      // [capacity]
+    PairOut *out;        // [capacity]
+    int capacity;
+};
+
+}  // namespace exx

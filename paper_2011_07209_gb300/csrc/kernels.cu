@@ -1,0 +1,850 @@
+// kernels.cu -- CUDA kernels of the EXX pair path for sm_103a.
+//
+//   k_tables       regular solid harmonics on PE points and far-field kernels
+//                  on shell points of one subdomain kind (Eqs. me, mepole)
+//   k_pair_rows    unique pair list, one CTA per orbital row (Step II)
+//   k_pair_scan    row offsets and per-cell ranges of the pair list
+//   k_pair_solve   persistent: one CTA owns one pair at a time and runs the
+//                  whole per-pair path (Steps III-V): pair density, moments,
+//                  far field, Poisson CG with the NK stencil, E / sigma
+//                  integrals and the D scatter
+//   k_finalize     ordered per-cell sums of E_xx, sigma and Pi
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "exx_dev.h"
+#include "kernels.h"
+
+namespace exx {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+__device__ __forceinline__ void unpack_m(int32_t p, int &m0, int &m1, int &m2)
+{
+    m0 = ((p >> 20) & 1023) - 512;
+    m1 = ((p >> 10) & 1023) - 512;
+    m2 = (p & 1023) - 512;
+}
+
+__device__ __forceinline__ int wrapi(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// Real solid harmonics r^l Y_lm from the Cartesian recurrences
+//   (x + i y)^m = A_m + i B_m,
+//   Q_m^m = (2m-1)!!,  Q_{m+1}^m = (2m+1) z Q_m^m,
+//   (l - m) Q_l^m = (2l-1) z Q_{l-1}^m - (l+m-1) r^2 Q_{l-2}^m,
+//   r^l Y_l0 = N_l0 Q_l^0,  r^l Y_{l,+-m} = sqrt2 N_lm Q_l^m {A_m, B_m},
+// N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), index l^2 + l + m.
+// ---------------------------------------------------------------------------
+__device__ void solid_harmonics(int lmax, double x, double y, double z, double *S)
+{
+    double A[7], B[7];
+    A[0] = 1.0;
+    B[0] = 0.0;
+    for (int m = 1; m <= lmax; ++m) {
+        A[m] = x * A[m - 1] - y * B[m - 1];
+        B[m] = x * B[m - 1] + y * A[m - 1];
+    }
+    const double r2 = x * x + y * y + z * z;
+    double Q[7][7];
+    double dfact = 1.0;
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) dfact *= (2.0 * m - 1.0);
+        Q[m][m] = dfact;
+        if (m + 1 <= lmax) Q[m + 1][m] = (2.0 * m + 1.0) * z * dfact;
+        for (int l = m + 2; l <= lmax; ++l)
+            Q[l][m] = ((2.0 * l - 1.0) * z * Q[l - 1][m] - (l + m - 1.0) * r2 * Q[l - 2][m]) / (double)(l - m);
+    }
+    for (int l = 0; l <= lmax; ++l) {
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0;   // (l-m)!/(l+m)!
+            for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+            const double nlm = sqrt((2.0 * l + 1.0) / kFourPi * ratio);
+            if (m == 0) {
+                S[l * l + l] = nlm * Q[l][0];
+            } else {
+                const double c = 1.4142135623730951 * nlm * Q[l][m];
+                S[l * l + l + m] = c * A[m];
+                S[l * l + l - m] = c * B[m];
+            }
+        }
+    }
+    for (int k = (lmax + 1) * (lmax + 1); k < kNlm; ++k) S[k] = 0.0;
+}
+
+__global__ void k_tables(const CellDev *__restrict__ cell, int which, double *S64, float *S32, double *T64,
+                         float *T32)
+{
+    const CellDev &C = *cell;
+    const SetDev &st = C.set[which];
+    const int total = st.n_pe + st.n_shell;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int m0, m1, m2;
+        if (q < st.n_pe) unpack_m(st.pe_m[q], m0, m1, m2);
+        else unpack_m(st.sh_m[q - st.n_pe], m0, m1, m2);
+        const double s0 = (double)m0 / C.n[0], s1 = (double)m1 / C.n[1], s2 = (double)m2 / C.n[2];
+        const double x = C.h[0][0] * s0 + C.h[0][1] * s1 + C.h[0][2] * s2;
+        const double y = C.h[1][0] * s0 + C.h[1][1] * s1 + C.h[1][2] * s2;
+        const double z = C.h[2][0] * s0 + C.h[2][1] * s1 + C.h[2][2] * s2;
+        double S[kNlm];
+        solid_harmonics(C.lmax, x, y, z, S);
+        if (q < st.n_pe) {
+            for (int k = 0; k < kNlm; ++k) {
+                S64[(size_t)q * kNlm + k] = S[k];
+                S32[(size_t)q * kNlm + k] = (float)S[k];
+            }
+        } else {
+            const int s = q - st.n_pe;
+            const double r = sqrt(x * x + y * y + z * z);
+            double rpow = r;          // r^(2l+1)
+            for (int l = 0; l < 7; ++l) {
+                const double f = (l <= C.lmax) ? kFourPi / ((2.0 * l + 1.0) * rpow) : 0.0;
+                for (int mm = -l; mm <= l; ++mm) {
+                    const double t = f * S[l * l + l + mm];
+                    T64[(size_t)(l * l + l + mm) * st.n_shell + s] = t;
+                    T32[(size_t)(l * l + l + mm) * st.n_shell + s] = (float)t;
+                }
+                rpow *= r * r;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair list.  For i <= j: s = h^-1 C (row sums left to right, no FMA);
+// ds = s_j - s_i - round(ds); image k in {-1,0,1}^3 with the smallest |h(ds+k)|^2
+// (first in lexicographic k on ties); kept when that is <= R_pair^2.  Centre
+// g = NINT(N (s_i + (ds + k)/2)) mod N, NINT rounding half away from zero.
+// These operations and their order are the written rule the oracle follows
+// too, so both lists agree bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dot3_rn(const double *r, double a, double b, double c)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(r[0], a), __dmul_rn(r[1], b)), __dmul_rn(r[2], c));
+}
+
+__device__ bool pair_test(const CellDev &C, int i, int j, int *kb, int *g)
+{
+    const double *ci = C.centres + 3 * i, *cj = C.centres + 3 * j;
+    double si[3], ds[3];
+    for (int al = 0; al < 3; ++al) {
+        si[al] = dot3_rn(C.hinv[al], ci[0], ci[1], ci[2]);
+        const double sj = dot3_rn(C.hinv[al], cj[0], cj[1], cj[2]);
+        const double d = __dadd_rn(sj, -si[al]);
+        ds[al] = __dadd_rn(d, -round(d));
+    }
+    double best = 1.0 / 0.0;
+    kb[0] = kb[1] = kb[2] = 0;
+    for (int k0 = -1; k0 <= 1; ++k0)
+        for (int k1 = -1; k1 <= 1; ++k1)
+            for (int k2 = -1; k2 <= 1; ++k2) {
+                const double t0 = __dadd_rn(ds[0], (double)k0), t1 = __dadd_rn(ds[1], (double)k1),
+                             t2 = __dadd_rn(ds[2], (double)k2);
+                const double d0 = dot3_rn(C.h[0], t0, t1, t2);
+                const double d1 = dot3_rn(C.h[1], t0, t1, t2);
+                const double d2 = dot3_rn(C.h[2], t0, t1, t2);
+                const double dd = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+                if (dd < best) {
+                    best = dd;
+                    kb[0] = k0;
+                    kb[1] = k1;
+                    kb[2] = k2;
+                }
+            }
+    if (!(best <= C.r_pair2)) return false;
+    for (int al = 0; al < 3; ++al) {
+        const double sm = __dadd_rn(si[al], __dmul_rn(__dadd_rn(ds[al], (double)kb[al]), 0.5));
+        const long long gg = (long long)round(__dmul_rn((double)C.n[al], sm));
+        long long r = gg % C.n[al];
+        if (r < 0) r += C.n[al];
+        g[al] = (int)r;
+    }
+    return true;
+}
+
+// One CTA of kRowThreads per orbital row (cell, i).  fill = 0: count; 1: write.
+__global__ void __launch_bounds__(kRowThreads) k_pair_rows(const CellDev *__restrict__ cells, int n_cells,
+                                                          ListDev L, int fill)
+{
+    const int row = blockIdx.x;
+    int c = 0;
+    while (c + 1 < n_cells && row >= cells[c + 1].row_base) ++c;
+    const CellDev &C = cells[c];
+    const int i = row - C.row_base;
+    if (i >= C.n_orb) return;
+    __shared__ int warp_tot[kRowThreads / 32];
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = fill ? L.row_start[row] : 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j0 = i; j0 < C.n_orb; j0 += kRowThreads) {
+        const int j = j0 + threadIdx.x;
+        int kb[3], g[3];
+        const bool ok = (j < C.n_orb) && pair_test(C, i, j, kb, g);
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) warp_tot[w] = __popc(bal);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int k = 0; k < kRowThreads / 32; ++k) {
+            if (k < w) before += warp_tot[k];
+            tot += warp_tot[k];
+        }
+        if (fill && ok) {
+            const int pos = s_base + before + __popc(bal & ((1u << lane) - 1u));
+            if (pos < L.capacity) {
+                PairRec pr;
+                pr.i = i;
+                pr.j = j;
+                pr.k[0] = kb[0];
+                pr.k[1] = kb[1];
+                pr.k[2] = kb[2];
+                pr.g[0] = g[0];
+                pr.g[1] = g[1];
+                pr.g[2] = g[2];
+                pr.cell = c;
+                pr.pad = 0;
+                L.pairs[pos] = pr;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
+    }
+    if (!fill && threadIdx.x == 0) L.row_count[row] = s_base;
+}
+
+// Exclusive scan of the row counts (single CTA), per-cell ranges, capacity check.
+__global__ void __launch_bounds__(1024) k_pair_scan(const CellDev *__restrict__ cells, int n_cells, int n_rows,
+                                                   ListDev L)
+{
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_rows; base += 1024) {
+        const int r = base + threadIdx.x;
+        const int v = r < n_rows ? L.row_count[r] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (r < n_rows) L.row_start[r] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int total = carry;
+        for (int c = 0; c < n_cells; ++c) {
+            const int r0 = cells[c].row_base;
+            const int r1 = r0 + cells[c].n_orb;
+            L.cell_start[c] = r0 < n_rows ? L.row_start[r0] : total;
+            L.cell_count[c] = (r1 < n_rows ? L.row_start[r1] : total) - L.cell_start[c];
+        }
+        *L.overflow = total > L.capacity ? 1 : 0;
+        *L.total = total > L.capacity ? 0 : total;
+        *L.queue = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions (fixed tree: deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum K values over the CTA; every thread receives the totals.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k] = warp_sum(v[k]);
+        if (lane == 0) red[w * K + k] = v[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nw ? red[lane * K + k] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) red[32 * K + k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
+}
+
+// Exact-product, double-float accumulation of FP32 dot products: the running
+// sum is hi + lo; each product a*b is split exactly as p + pe by an FMA and
+// added with TwoSum, so per-thread partial sums carry ~48 significant bits.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_fma(DF &acc, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fadd_rn(s, -acc.hi);
+    const float err = __fadd_rn(__fadd_rn(acc.hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, pe));
+}
+__device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
+// Orbital access.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double phi_at(const CellDev &C, int o, int g0, int g1, int g2)
+{
+    const int32_t *lo = C.box_lo + 3 * o;
+    const int u0 = wrapi(g0 - lo[0], C.n[0]);
+    const int u1 = wrapi(g1 - lo[1], C.n[1]);
+    const int u2 = wrapi(g2 - lo[2], C.n[2]);
+    if (u0 >= C.box[0] || u1 >= C.box[1] || u2 >= C.box[2]) return 0.0;
+    return __ldg(C.phi + (((size_t)o * C.box[0] + u0) * C.box[1] + u1) * C.box[2] + u2);
+}
+
+// D^o(g) += val, with the D-box membership check.  Returns false when a
+// non-zero value falls outside the box.
+__device__ __forceinline__ bool d_add(const CellDev &C, int o, int g0, int g1, int g2, double val)
+{
+    const int32_t *lo = C.dbox_lo + 3 * o;
+    const int u0 = wrapi(g0 - lo[0], C.n[0]);
+    const int u1 = wrapi(g1 - lo[1], C.n[1]);
+    const int u2 = wrapi(g2 - lo[2], C.n[2]);
+    if (u0 >= C.dbox[0] || u1 >= C.dbox[1] || u2 >= C.dbox[2]) return val == 0.0;
+    atomicAdd(C.dxx + (((size_t)o * C.dbox[0] + u0) * C.dbox[1] + u1) * C.dbox[2] + u2, val);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Stencil:  (L f)(off) = sum_d sum_{s=-n..n} cw[d][|s|] f(off + s stride_d).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T lap_at(const T *__restrict__ f, int off, const T (*cw)[8], const int *ds, int ndir,
+                                    int n, T center)
+{
+    T acc = center * f[off];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (d < ndir) {
+            const int st = ds[d];
+#pragma unroll
+            for (int s = 1; s <= 6; ++s)
+                if (s <= n) acc += cw[d][s] * (f[off + s * st] + f[off - s * st]);
+        }
+    }
+    return acc;
+}
+
+// r = 4 pi rho + L v on PE (v: x on PE, far field on the halo); returns sum r^2.
+__device__ double residual_pass(const SetDev &S, const double *__restrict__ vbox, const double *__restrict__ rho,
+                                double *__restrict__ r64, const double (*cw)[8], const int *ds, int ndir, int n,
+                                double center, double *red)
+{
+    double acc[1] = {0.0};
+    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        const double r = kFourPi * rho[k] + lap_at<double>(vbox, off, cw, ds, ndir, n, center);
+        r64[k] = r;
+        acc[0] += r * r;
+    }
+    block_sum<1>(acc, red);
+    return acc[0];
+}
+
+struct SlotWork {
+    char *base;
+    size_t slot_bytes;
+    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e;
+};
+
+// Shared per-CTA state.
+struct SmemCell {
+    CellDev C;
+    double cw64[6][8];
+    float cw32[6][8];
+    double Q[kNlm];
+    float Qf[kNlm];
+    double center64;
+    float center32;
+    int ds[6];
+};
+
+template <class T>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
+                                                                 SlotWork W, int inner_shift)
+{
+    __shared__ SmemCell sm;
+    __shared__ double red[33 * 10 + 64];
+    __shared__ double qpart[kSolveThreads / 32][kNlm];
+    __shared__ int s_pair, s_cell, s_flag;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    char *slot = W.base + (size_t)blockIdx.x * W.slot_bytes;
+    double *vbox = (double *)(slot + W.off_vbox);
+    T *pbox = (T *)(slot + W.off_pbox);
+    double *rho = (double *)(slot + W.off_rho);
+    double *r64 = (double *)(slot + W.off_r64);
+    T *rv = (T *)(slot + W.off_r);
+    T *qv = (T *)(slot + W.off_q);
+    T *ev = (T *)(slot + W.off_e);
+    const bool mixed = sizeof(T) == 4;
+    const double inner_red = ldexp(1.0, -inner_shift);   // inner FP32 solve residual reduction
+
+    if (tid == 0) s_cell = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_pair = atomicAdd(L.queue, 1);
+        __syncthreads();
+        const int t = s_pair;
+        if (t >= *L.total) break;
+        const PairRec pr = L.pairs[t];
+        if (pr.cell != s_cell) {
+            // load the cell constants into shared memory
+            const int *src = (const int *)&cells[pr.cell];
+            int *dst = (int *)&sm.C;
+            for (int k = tid; k < (int)(sizeof(CellDev) / sizeof(int)); k += nt) dst[k] = src[k];
+            __syncthreads();
+            if (tid < 48) {
+                const int d = tid / 8, s = tid % 8;
+                sm.cw64[d][s] = sm.C.cw64[d][s];
+                sm.cw32[d][s] = sm.C.cw32[d][s];
+            }
+            if (tid == 0) {
+                double c = 0.0;
+                for (int d = 0; d < sm.C.ndir; ++d) c += sm.C.cw64[d][0];
+                sm.center64 = c;
+                sm.center32 = (float)c;
+                s_cell = pr.cell;
+            }
+            __syncthreads();
+        }
+        const CellDev &C = sm.C;
+        const int self = (pr.i == pr.j);
+        const SetDev &S = C.set[self ? 0 : 1];
+        if (tid < 6) sm.ds[tid] = S.dstride[tid];
+        if (tid == 0) s_flag = 0;
+        const int ndir = C.ndir, fdn = C.fd_n;
+
+        // ---- Step III: pair density on PE, g = MOD(g_ij + m, N) (Eq. l2g) ----
+        for (int k = tid; k < S.n_pe; k += nt) {
+            int m0, m1, m2;
+            unpack_m(S.pe_m[k], m0, m1, m2);
+            const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
+                      g2 = wrapi(pr.g[2] + m2, C.n[2]);
+            rho[k] = phi_at(C, pr.i, g0, g1, g2) * phi_at(C, pr.j, g0, g1, g2);
+        }
+        __syncthreads();
+
+        // ---- multipole moments Q_lm = dV sum_PE rho r^l Y_lm (Eq. mepole) ----
+        {
+            double a0 = 0.0, a1 = 0.0;
+            const int nchunk = (S.n_pe + 31) >> 5;
+            for (int ch = warp; ch < nchunk; ch += nwarps) {
+                const int k0 = ch << 5;
+                const double rl = (k0 + lane < S.n_pe) ? rho[k0 + lane] : 0.0;
+                const int cnt = min(32, S.n_pe - k0);
+                if (mixed) {
+                    float f0 = 0.f, f1 = 0.f;
+                    const float rlf = (float)rl;
+                    for (int p = 0; p < cnt; ++p) {
+                        const float rp = __shfl_sync(0xffffffffu, rlf, p);
+                        const float *row = S.S32 + (size_t)(k0 + p) * kNlm;
+                        f0 += rp * row[lane];
+                        if (lane + 32 < kNlm) f1 += rp * row[lane + 32];
+                    }
+                    a0 += f0;
+                    a1 += f1;
+                } else {
+                    for (int p = 0; p < cnt; ++p) {
+                        const double rp = __shfl_sync(0xffffffffu, rl, p);
+                        const double *row = S.S64 + (size_t)(k0 + p) * kNlm;
+                        a0 += rp * row[lane];
+                        if (lane + 32 < kNlm) a1 += rp * row[lane + 32];
+                    }
+                }
+            }
+            qpart[warp][lane] = a0;
+            if (lane + 32 < kNlm) qpart[warp][lane + 32] = a1;
+            __syncthreads();
+            if (tid < kNlm) {
+                double s = 0.0;
+                for (int w = 0; w < nwarps; ++w) s += qpart[w][tid];
+                const double q = (tid < (C.lmax + 1) * (C.lmax + 1)) ? s * C.dv : 0.0;
+                sm.Q[tid] = q;
+                sm.Qf[tid] = (float)q;
+            }
+            __syncthreads();
+        }
+
+        // ---- far field on the halo (Eq. me): Dirichlet data in vbox ----
+        for (int h = tid; h < S.n_halo; h += nt) {
+            double v = 0.0;
+            if (mixed) {
+                float vf = 0.f;
+                for (int lm = 0; lm < kNlm; ++lm) vf += sm.Qf[lm] * S.T32[(size_t)lm * S.n_shell + h];
+                v = vf;
+            } else {
+                for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * S.T64[(size_t)lm * S.n_shell + h];
+            }
+            vbox[S.halo_off[h]] = v;
+        }
+        __syncthreads();
+
+        // ---- Step IV: Poisson solve (Eq. pe) ----
+        double rr2 = residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red);
+        const double bn = sqrt(rr2);
+        const double stop = C.tol * bn;
+        int iters = 0, refine = 1, status = 0;
+        double rnorm = bn;
+        if (!mixed) {
+            // plain FP64 CG: x in vbox (PE), r in r64, p in pbox, q in qv
+            double *pd = (double *)pbox;
+            double *qd = (double *)qv;
+            double rr = rr2;
+            if (bn > 0.0) {
+                for (int k = tid; k < S.n_pe; k += nt) pd[S.pe_off[k]] = r64[k];
+                __syncthreads();
+                for (;;) {
+                    if (sqrt(rr) <= stop) {
+                        rr = residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red);
+                        ++refine;
+                        if (sqrt(rr) <= stop) break;
+                        for (int k = tid; k < S.n_pe; k += nt) pd[S.pe_off[k]] = r64[k];
+                        __syncthreads();
+                    }
+                    if (iters >= C.max_iter) {
+                        status = 5;
+                        break;
+                    }
+                    double pq[1] = {0.0};
+                    for (int k = tid; k < S.n_pe; k += nt) {
+                        const int off = S.pe_off[k];
+                        const double q = -lap_at<double>(pd, off, sm.cw64, sm.ds, ndir, fdn, sm.center64);
+                        qd[k] = q;
+                        pq[0] += pd[off] * q;
+                    }
+                    block_sum<1>(pq, red);
+                    const double alpha = rr / pq[0];
+                    double rn[1] = {0.0};
+                    for (int k = tid; k < S.n_pe; k += nt) {
+                        const int off = S.pe_off[k];
+                        vbox[off] += alpha * pd[off];
+                        const double r = r64[k] - alpha * qd[k];
+                        r64[k] = r;
+                        rn[0] += r * r;
+                    }
+                    block_sum<1>(rn, red);
+                    const double beta = rn[0] / rr;
+                    rr = rn[0];
+                    for (int k = tid; k < S.n_pe; k += nt) {
+                        const int off = S.pe_off[k];
+                        pd[off] = r64[k] + beta * pd[off];
+                    }
+                    ++iters;
+                    __syncthreads();
+                }
+                rnorm = sqrt(rr);
+            }
+        } else {
+            // mixed: FP32 CG on the correction inside an FP64-residual refinement loop
+            float *pf = (float *)pbox;
+            float *rf = (float *)rv;
+            float *qf = (float *)qv;
+            float *ef = (float *)ev;
+            while (bn > 0.0 && rnorm > stop) {
+                if (iters >= C.max_iter) {
+                    status = 5;
+                    break;
+                }
+                double rr0[1] = {0.0};
+                {
+                    DF a = {0.f, 0.f};
+                    for (int k = tid; k < S.n_pe; k += nt) {
+                        const float r = (float)r64[k];
+                        rf[k] = r;
+                        ef[k] = 0.f;
+                        pf[S.pe_off[k]] = r;
+                        df_fma(a, r, r);
+                    }
+                    rr0[0] = df_val(a);
+                }
+                block_sum<1>(rr0, red);
+                double rr = rr0[0];
+                const double inner_stop = fmax(inner_red * sqrt(rr), 0.5 * stop);
+                for (;;) {
+                    double pq[1];
+                    {
+                        DF a = {0.f, 0.f};
+                        for (int k = tid; k < S.n_pe; k += nt) {
+                            const int off = S.pe_off[k];
+                            const float q = -lap_at<float>(pf, off, sm.cw32, sm.ds, ndir, fdn, sm.center32);
+                            qf[k] = q;
+                            df_fma(a, pf[off], q);
+                        }
+                        pq[0] = df_val(a);
+                    }
+                    block_sum<1>(pq, red);
+                    const float alpha = (float)(rr / pq[0]);
+                    double rn[1];
+                    {
+                        DF a = {0.f, 0.f};
+                        for (int k = tid; k < S.n_pe; k += nt) {
+                            const int off = S.pe_off[k];
+                            ef[k] += alpha * pf[off];
+                            const float r = rf[k] - alpha * qf[k];
+                            rf[k] = r;
+                            df_fma(a, r, r);
+                        }
+                        rn[0] = df_val(a);
+                    }
+                    block_sum<1>(rn, red);
+                    ++iters;
+                    if (sqrt(rn[0]) <= inner_stop || iters >= C.max_iter) break;
+                    const float beta = (float)(rn[0] / rr);
+                    rr = rn[0];
+                    for (int k = tid; k < S.n_pe; k += nt) {
+                        const int off = S.pe_off[k];
+                        pf[off] = rf[k] + beta * pf[off];
+                    }
+                    __syncthreads();
+                }
+                for (int k = tid; k < S.n_pe; k += nt) vbox[S.pe_off[k]] += (double)ef[k];
+                __syncthreads();
+                rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+                ++refine;
+            }
+        }
+
+        // ---- Step V: energy and stress integrals (Eqs. exxGen_mlwf, sxx_working, d1_1) ----
+        double acc[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+        for (int k = tid; k < S.n_pe; k += nt) {
+            const int off = S.pe_off[k];
+            const double rk = rho[k];
+            const double v = vbox[off];
+            acc[0] += rk * v;
+            double dxi[3];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                const int st = S.gstride[al];
+                double t = 0.0;
+#pragma unroll
+                for (int s = 1; s <= 6; ++s)
+                    if (s <= fdn) t += C.w1dx[al][s] * (vbox[off + s * st] - vbox[off - s * st]);
+                dxi[al] = t;
+            }
+            int m0, m1, m2;
+            unpack_m(S.pe_m[k], m0, m1, m2);
+            const double sb[3] = {(double)m0 / C.n[0], (double)m1 / C.n[1], (double)m2 / C.n[2]};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double dva = C.J[a][0] * dxi[0] + C.J[a][1] * dxi[1] + C.J[a][2] * dxi[2];
+                const double rdv = rk * dva;
+#pragma unroll
+                for (int al = 0; al < 3; ++al) acc[1 + 3 * a + al] += sb[al] * rdv;
+            }
+        }
+        block_sum<10>(acc, red);
+
+        // ---- D^i += v phi_j, D^j += v phi_i on PE and shell (Eq. Dxx, Step V) ----
+        if (C.dxx) {
+            bool ok = true;
+            for (int k = tid; k < S.n_pe + S.n_shell; k += nt) {
+                int m0, m1, m2;
+                double v;
+                if (k < S.n_pe) {
+                    unpack_m(S.pe_m[k], m0, m1, m2);
+                    v = vbox[S.pe_off[k]];
+                } else {
+                    const int s = k - S.n_pe;
+                    unpack_m(S.sh_m[s], m0, m1, m2);
+                    if (mixed) {
+                        float vf = 0.f;
+                        for (int lm = 0; lm < kNlm; ++lm) vf += sm.Qf[lm] * S.T32[(size_t)lm * S.n_shell + s];
+                        v = vf;
+                    } else {
+                        v = 0.0;
+                        for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * S.T64[(size_t)lm * S.n_shell + s];
+                    }
+                }
+                const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
+                          g2 = wrapi(pr.g[2] + m2, C.n[2]);
+                const double fj = phi_at(C, pr.j, g0, g1, g2);
+                ok &= d_add(C, pr.i, g0, g1, g2, v * fj);
+                if (!self) {
+                    const double fi = phi_at(C, pr.i, g0, g1, g2);
+                    ok &= d_add(C, pr.j, g0, g1, g2, v * fi);
+                }
+            }
+            if (!ok) s_flag = 1;
+        }
+
+        // ---- restore the all-zero boxes for the next pair ----
+        __syncthreads();
+        for (int k = tid; k < S.n_pe; k += nt) {
+            const int off = S.pe_off[k];
+            vbox[off] = 0.0;
+            pbox[off] = (T)0;
+        }
+        for (int h = tid; h < S.n_halo; h += nt) vbox[S.halo_off[h]] = 0.0;
+        if (tid == 0) {
+            PairOut o;
+            o.e = acc[0] * C.dv;
+            for (int k = 0; k < 9; ++k) o.sig[k] = acc[1 + k] * C.dv;
+            o.iters = iters;
+            o.refine = refine;
+            o.status = status ? status : (s_flag ? 7 : 0);
+            o.pad = 0;
+            L.out[t] = o;
+        }
+        (void)rnorm;
+    }
+}
+
+// Ordered per-cell reductions (Eqs. exxGen_mlwf, sxx_working, pixx_working).
+__global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ cells, ListDev L, CellResult *res)
+{
+    const int c = blockIdx.x;
+    const CellDev &C = cells[c];
+    __shared__ double red[33 * 10 + 64];
+    __shared__ int s_fail, s_status, s_maxit, s_maxref;
+    __shared__ unsigned long long s_tot, s_tref;
+    if (threadIdx.x == 0) {
+        s_fail = 0x7fffffff;
+        s_status = 0;
+        s_maxit = 0;
+        s_maxref = 0;
+        s_tot = 0ull;
+        s_tref = 0ull;
+    }
+    __syncthreads();
+    const int start = *L.overflow ? 0 : L.cell_start[c];
+    const int cnt = *L.overflow ? 0 : L.cell_count[c];
+    double acc[10];
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    // contiguous chunks per thread: a fixed summation order
+    const int per = (cnt + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * per, p1 = min(cnt, p0 + per);
+    long long tot = 0, tref = 0;
+    int maxit = 0, maxref = 0, fail = 0x7fffffff, status = 0;
+    for (int p = p0; p < p1; ++p) {
+        const PairRec pr = L.pairs[start + p];
+        const PairOut o = L.out[start + p];
+        const double w = (pr.i == pr.j) ? 1.0 : 2.0;
+        acc[0] += w * o.e;
+        for (int k = 0; k < 9; ++k) acc[1 + k] += w * o.sig[k];
+        tot += o.iters;
+        tref += o.refine;
+        maxit = max(maxit, o.iters);
+        maxref = max(maxref, o.refine);
+        if (o.status && p < fail) {
+            fail = p;
+            status = o.status;
+        }
+    }
+    block_sum<10>(acc, red);
+    atomicMax(&s_maxit, maxit);
+    atomicMax(&s_maxref, maxref);
+    atomicAdd(&s_tot, (unsigned long long)tot);
+    atomicAdd(&s_tref, (unsigned long long)tref);
+    atomicMin(&s_fail, fail);
+    __syncthreads();
+    if (fail == s_fail && fail != 0x7fffffff) s_status = status;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CellResult r;
+        r.e_xx = -acc[0];
+        for (int k = 0; k < 9; ++k) r.dedh[k] = -2.0 * acc[1 + k];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int al = 0; al < 3; ++al) s += r.dedh[3 * a + al] * C.h[b][al];
+                r.stress[3 * a + b] = -s / C.vol;
+            }
+        r.total_iter = (long long)s_tot;
+        r.total_refine = (long long)s_tref;
+        r.n_pairs = cnt;
+        r.status = *L.overflow ? 6 : s_status;
+        r.failed_pair = (s_fail == 0x7fffffff) ? -1 : s_fail;
+        r.max_iter = s_maxit;
+        r.max_refine = s_maxref;
+        r.pad = 0;
+        res[c] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch wrappers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_tables(const CellDev *cell, int which, int n_points, double *S64, float *S32, double *T64,
+                          float *T32, cudaStream_t s)
+{
+    const int threads = 128;
+    const int blocks = (n_points + threads - 1) / threads;
+    if (blocks > 0) k_tables<<<blocks, threads, 0, s>>>(cell, which, S64, S32, T64, T32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_list(const CellDev *cells, int n_cells, int n_rows, const ListDev &L, cudaStream_t s)
+{
+    if (n_rows > 0) k_pair_rows<<<n_rows, kRowThreads, 0, s>>>(cells, n_cells, L, 0);
+    k_pair_scan<<<1, 1024, 0, s>>>(cells, n_cells, n_rows, L);
+    if (n_rows > 0) k_pair_rows<<<n_rows, kRowThreads, 0, s>>>(cells, n_cells, L, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlots &slots, bool mixed,
+                         int inner_shift, cudaStream_t s)
+{
+    SlotWork W;
+    W.base = slots.base;
+    W.slot_bytes = slots.slot_bytes;
+    W.off_vbox = slots.off_vbox;
+    W.off_pbox = slots.off_pbox;
+    W.off_rho = slots.off_rho;
+    W.off_r64 = slots.off_r64;
+    W.off_r = slots.off_r;
+    W.off_q = slots.off_q;
+    W.off_e = slots.off_e;
+    if (mixed) k_pair_solve<float><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
+    else k_pair_solve<double><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const CellDev *cells, int n_cells, const ListDev &L, CellResult *res, cudaStream_t s)
+{
+    k_finalize<<<n_cells, 256, 0, s>>>(cells, L, res);
+    return cudaGetLastError();
+}
+
+}  // namespace exx
+
+namespace exx {
+int solve_blocks_per_sm(bool mixed)
+{
+    int n = 0;
+    if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair_solve<float>, kSolveThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair_solve<double>, kSolveThreads, 0);
+    return n;
+}
+}  // namespace exx

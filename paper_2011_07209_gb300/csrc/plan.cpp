@@ -1,0 +1,446 @@
+// plan.cpp -- host geometry of the EXX pair path.
+//
+// Cell metric (Sec. II B 1, Eqs. s_to_xi, jacb, lapG_), Natan-Kronik stencil
+// with auxiliary grid directions (Eqs. nk2d_aux, kappa_def, nk3d_mu,
+// nk3d_Mb_f, lapG_mod_nk3d, Algorithm 1), central-difference weights
+// (Eqs. d2_1, d1_1) and proto-subdomain offset sets (Eqs. rbar, g0).
+//
+// Compiled with -ffp-contract=off: the PE / shell membership test and h^-1
+// are integer-deciding arithmetic and follow a fixed operation order.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/exx.h"
+
+namespace exx {
+
+int make_metric(const double lattice[3][3], const int n[3], Metric &m)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int al = 0; al < 3; ++al) m.h[a][al] = lattice[al][a];
+    const double(*h)[3] = m.h;
+    // det and adjugate, left-to-right products and sums
+    const double c00 = h[1][1] * h[2][2] - h[1][2] * h[2][1];
+    const double c01 = h[1][0] * h[2][2] - h[1][2] * h[2][0];
+    const double c02 = h[1][0] * h[2][1] - h[1][1] * h[2][0];
+    const double det = h[0][0] * c00 - h[0][1] * c01 + h[0][2] * c02;
+    if (!(det > 0.0) || !std::isfinite(det)) return EXX_ERR_CELL;
+    m.hinv[0][0] = c00 / det;
+    m.hinv[0][1] = (h[0][2] * h[2][1] - h[0][1] * h[2][2]) / det;
+    m.hinv[0][2] = (h[0][1] * h[1][2] - h[0][2] * h[1][1]) / det;
+    m.hinv[1][0] = (h[1][2] * h[2][0] - h[1][0] * h[2][2]) / det;
+    m.hinv[1][1] = (h[0][0] * h[2][2] - h[0][2] * h[2][0]) / det;
+    m.hinv[1][2] = (h[0][2] * h[1][0] - h[0][0] * h[1][2]) / det;
+    m.hinv[2][0] = c02 / det;
+    m.hinv[2][1] = (h[0][1] * h[2][0] - h[0][0] * h[2][1]) / det;
+    m.hinv[2][2] = (h[0][0] * h[1][1] - h[0][1] * h[1][0]) / det;
+    m.vol = det;
+    for (int al = 0; al < 3; ++al) {
+        if (n[al] < 1) return EXX_ERR_ARG;
+        m.n[al] = n[al];
+        m.len[al] = std::sqrt(h[0][al] * h[0][al] + h[1][al] * h[1][al] + h[2][al] * h[2][al]);
+        m.dxi[al] = m.len[al] / n[al];
+    }
+    m.dv = det / ((double)n[0] * n[1] * n[2]);
+    for (int a = 0; a < 3; ++a)
+        for (int al = 0; al < 3; ++al) m.J[a][al] = m.len[al] * m.hinv[al][a];
+    for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be)
+            m.F[al][be] = m.J[0][al] * m.J[0][be] + m.J[1][al] * m.J[1][be] + m.J[2][al] * m.J[2][be];
+    return EXX_OK;
+}
+
+// r = h (m / N): the offset vector of a grid step, fixed operation order.
+static inline void step_vec(const Metric &mt, const int *m, double *r)
+{
+    const double s0 = (double)m[0] / (double)mt.n[0];
+    const double s1 = (double)m[1] / (double)mt.n[1];
+    const double s2 = (double)m[2] / (double)mt.n[2];
+    for (int a = 0; a < 3; ++a) r[a] = mt.h[a][0] * s0 + mt.h[a][1] * s1 + mt.h[a][2] * s2;
+}
+
+static inline double step_len(const Metric &mt, const int *m)
+{
+    double r[3];
+    step_vec(mt, m, r);
+    return std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+}
+
+void fd_weights(int n, double *w2, double *w1)
+{
+    // Moment conditions of the central (2n+1)-point formulas solved by Gaussian
+    // elimination in long double.
+    long double A[kMaxFd + 1][kMaxFd + 2];
+    // second derivative: unknowns w_0..w_n, moments k = 0, 2, ..., 2n
+    for (int r = 0; r <= n; ++r) {
+        const int k = 2 * r;
+        for (int q = 0; q <= n; ++q) {
+            if (q == 0) A[r][q] = (k == 0) ? 1.0L : 0.0L;
+            else A[r][q] = 2.0L * std::pow((long double)q, (long double)k);
+        }
+        A[r][n + 1] = (k == 2) ? 2.0L : 0.0L;
+    }
+    auto solve = [](long double (*M)[kMaxFd + 2], int sz, long double *x) {
+        for (int c = 0; c < sz; ++c) {
+            int p = c;
+            for (int r = c + 1; r < sz; ++r)
+                if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+            for (int k = 0; k <= sz; ++k) std::swap(M[c][k], M[p][k]);
+            for (int r = 0; r < sz; ++r) {
+                if (r == c) continue;
+                const long double f = M[r][c] / M[c][c];
+                for (int k = c; k <= sz; ++k) M[r][k] -= f * M[c][k];
+            }
+        }
+        for (int c = 0; c < sz; ++c) x[c] = M[c][sz] / M[c][c];
+    };
+    long double x[kMaxFd + 1];
+    solve(A, n + 1, x);
+    for (int q = 0; q <= n; ++q) w2[q] = (double)x[q];
+    // first derivative: unknowns w_1..w_n, moments k = 1, 3, ..., 2n-1
+    long double B[kMaxFd + 1][kMaxFd + 2];
+    for (int r = 0; r < n; ++r) {
+        const int k = 2 * r + 1;
+        for (int q = 1; q <= n; ++q) B[r][q - 1] = 2.0L * std::pow((long double)q, (long double)k);
+        B[r][n] = 0.0L;
+    }
+    // move rhs into column n (size n system)
+    for (int r = 0; r < n; ++r) {
+        const int k = 2 * r + 1;
+        B[r][n] = (k == 1) ? 1.0L : 0.0L;
+    }
+    long double y[kMaxFd + 1];
+    {
+        long double Mx[kMaxFd + 1][kMaxFd + 2];
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c <= n; ++c) Mx[r][c] = B[r][c];
+        solve(Mx, n, y);
+    }
+    w1[0] = 0.0;
+    for (int q = 1; q <= n; ++q) w1[q] = (double)y[q - 1];
+}
+
+namespace {
+
+struct Cand {
+    int m[3];
+    double len;
+};
+
+bool cand_less(const Cand &x, const Cand &y)
+{
+    if (x.len != y.len) return x.len < y.len;
+    for (int k = 0; k < 3; ++k)
+        if (x.m[k] != y.m[k]) return x.m[k] < y.m[k];
+    return false;
+}
+
+// The sorted list of candidate non-axial grid directions (input of Algorithm
+// 1): shells of max_alpha |m_alpha| = S swept outward; the sweep ends after the
+// first shell S >= 2 lying wholly beyond the longest first-shell spacing.
+std::vector<Cand> candidates(const Metric &mt, int nq)
+{
+    std::vector<Cand> out;
+    double first_shell_max = 0.0;
+    for (int S = 1; S <= 8; ++S) {
+        double shell_min = HUGE_VAL;
+        for (int i = -S; i <= S; ++i)
+            for (int j = -S; j <= S; ++j)
+                for (int k = -S; k <= S; ++k) {
+                    if (std::max(std::abs(i), std::max(std::abs(j), std::abs(k))) != S) continue;
+                    const int m[3] = {i, j, k};
+                    const double l = step_len(mt, m);
+                    if (S == 1) first_shell_max = std::max(first_shell_max, l);
+                    shell_min = std::min(shell_min, l);
+                    const int nz = (i != 0) + (j != 0) + (k != 0);
+                    const int lead = i != 0 ? i : (j != 0 ? j : k);
+                    if (nz >= 2 && lead > 0) out.push_back(Cand{{i, j, k}, l});
+                }
+        if (S >= 2 && shell_min > first_shell_max) break;
+    }
+    std::sort(out.begin(), out.end(), cand_less);
+    if ((int)out.size() > nq) out.resize(nq);
+    return out;
+}
+
+void unit_coeffs(const Metric &mt, const int *m, double *a, double *len)
+{
+    const double l = step_len(mt, m);
+    for (int al = 0; al < 3; ++al) a[al] = (double)m[al] * mt.dxi[al] / l;
+    *len = l;
+}
+
+double det3(const double M[3][3])
+{
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+}
+
+// Algorithm 1 of the paper on the candidate list.
+int choose_aux(const Metric &mt, const std::vector<Cand> &cands, int aux[3][3])
+{
+    double col[3][3] = {};
+    int p = 0;
+    for (const Cand &c : cands) {
+        double a[3], l;
+        unit_coeffs(mt, c.m, a, &l);
+        col[p][0] = a[0] * a[1];
+        col[p][1] = a[0] * a[2];
+        col[p][2] = a[1] * a[2];
+        bool ok;
+        if (p == 0) {
+            ok = true;
+        } else if (p == 1) {
+            const double d = col[0][0] * col[1][0] + col[0][1] * col[1][1] + col[0][2] * col[1][2];
+            const double n0 = col[0][0] * col[0][0] + col[0][1] * col[0][1] + col[0][2] * col[0][2];
+            const double n1 = col[1][0] * col[1][0] + col[1][1] * col[1][1] + col[1][2] * col[1][2];
+            ok = std::fabs(d) < (1.0 - 1e-8) * std::sqrt(n0 * n1);
+        } else {
+            double M[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) M[r][s] = col[s][r];
+            const double scale = std::sqrt(col[0][0] * col[0][0] + col[0][1] * col[0][1] + col[0][2] * col[0][2]) *
+                                 std::sqrt(col[1][0] * col[1][0] + col[1][1] * col[1][1] + col[1][2] * col[1][2]) *
+                                 std::sqrt(col[2][0] * col[2][0] + col[2][1] * col[2][1] + col[2][2] * col[2][2]);
+            ok = std::fabs(det3(M)) > 1e-10 * scale;
+        }
+        if (ok) {
+            for (int k = 0; k < 3; ++k) aux[p][k] = c.m[k];
+            if (++p == 3) return EXX_OK;
+        }
+    }
+    return EXX_ERR_NK;
+}
+
+// Symbol of the operator at wave vector t: sum_dir coef (w0 + 2 sum_q w_q cos(q t.d)).
+bool negative_definite(const Stencil &st, int n)
+{
+    double w2[kMaxFd + 1], w1[kMaxFd + 1];
+    fd_weights(n, w2, w1);
+    const int G = 32;
+    const double two_pi = 6.283185307179586;
+    for (int i = 0; i < G; ++i)
+        for (int j = 0; j < G; ++j)
+            for (int k = 0; k < G; ++k) {
+                if (!i && !j && !k) continue;
+                const double t0 = two_pi * i / G, t1 = two_pi * j / G, t2 = two_pi * k / G;
+                double s = 0.0;
+                for (int d = 0; d < st.ndir; ++d) {
+                    const double ph = t0 * st.dir[d][0] + t1 * st.dir[d][1] + t2 * st.dir[d][2];
+                    double sym = w2[0];
+                    for (int q = 1; q <= n; ++q) sym += 2.0 * w2[q] * std::cos(q * ph);
+                    s += st.coef[d] * sym;
+                }
+                if (!(s < 0.0)) return false;
+            }
+    return true;
+}
+
+}  // namespace
+
+int make_stencil(const Metric &mt, int fd_n, int nq, const int (*aux_in)[3], int n_aux_fixed, Stencil &st)
+{
+    st = Stencil();
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    const double fdiag = std::max(mt.F[0][0], std::max(mt.F[1][1], mt.F[2][2]));
+    int last_off = -1;
+    for (int k = 0; k < 3; ++k)
+        if (std::fabs(mt.F[pa[k]][pb[k]]) > 1e-12 * fdiag) {
+            ++st.n_off;
+            last_off = k;
+        }
+    int aux[3][3] = {};
+    int n_aux = 0;
+    if (aux_in) {
+        n_aux = n_aux_fixed;
+        for (int p = 0; p < n_aux; ++p)
+            for (int k = 0; k < 3; ++k) aux[p][k] = aux_in[p][k];
+    } else if (st.n_off == 1) {
+        // grid-resolved bisector L' ~ L^_alpha + kappa L^_beta (Eqs. nk2d_aux, kappa_def)
+        const int al = pa[last_off], be = pb[last_off];
+        const double dotab = mt.h[0][al] * mt.h[0][be] + mt.h[1][al] * mt.h[1][be] + mt.h[2][al] * mt.h[2][be];
+        aux[0][al] = 1;
+        aux[0][be] = dotab > 0.0 ? -1 : 1;
+        n_aux = 1;
+    } else if (st.n_off >= 2) {
+        if (choose_aux(mt, candidates(mt, nq), aux) != EXX_OK) return EXX_ERR_NK;
+        n_aux = 3;
+    }
+    double a[3][3] = {}, len[3] = {};
+    for (int p = 0; p < n_aux; ++p) unit_coeffs(mt, aux[p], a[p], &len[p]);
+    double b[3] = {};
+    if (n_aux == 1) {
+        int al = -1, be = -1;
+        for (int k = 0; k < 3; ++k)
+            if (aux[0][pa[k]] != 0 && aux[0][pb[k]] != 0) {
+                al = pa[k];
+                be = pb[k];
+            }
+        if (al < 0) return EXX_ERR_NK;
+        b[0] = mt.F[al][be] / (a[0][al] * a[0][be]);
+        for (int k = 0; k < 3; ++k) {
+            if (pa[k] == al && pb[k] == be) continue;
+            if (std::fabs(mt.F[pa[k]][pb[k]] - b[0] * a[0][pa[k]] * a[0][pb[k]]) > 1e-12 * fdiag) return EXX_ERR_NK;
+        }
+    } else if (n_aux == 3) {
+        // M b = (F12, F13, F23), Eq. nk3d_Mb_f; Gaussian elimination with pivoting
+        double M[3][4];
+        for (int p = 0; p < 3; ++p) {
+            M[0][p] = a[p][0] * a[p][1];
+            M[1][p] = a[p][0] * a[p][2];
+            M[2][p] = a[p][1] * a[p][2];
+        }
+        M[0][3] = mt.F[0][1];
+        M[1][3] = mt.F[0][2];
+        M[2][3] = mt.F[1][2];
+        for (int c = 0; c < 3; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < 3; ++r)
+                if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+            if (M[piv][c] == 0.0) return EXX_ERR_NK;
+            for (int k = 0; k < 4; ++k) std::swap(M[c][k], M[piv][k]);
+            for (int r = c + 1; r < 3; ++r) {
+                const double f = M[r][c] / M[c][c];
+                for (int k = c; k < 4; ++k) M[r][k] -= f * M[c][k];
+            }
+        }
+        for (int r = 2; r >= 0; --r) {
+            double s = M[r][3];
+            for (int k = r + 1; k < 3; ++k) s -= M[r][k] * b[k];
+            b[r] = s / M[r][r];
+        }
+    } else if (n_aux != 0) {
+        return EXX_ERR_NK;
+    }
+    if (n_aux == 0 && st.n_off != 0) return EXX_ERR_NK;
+    st.n_aux = n_aux;
+    st.ndir = 3 + n_aux;
+    for (int al = 0; al < 3; ++al) {
+        double c = mt.F[al][al];
+        for (int p = 0; p < n_aux; ++p) c -= b[p] * a[p][al] * a[p][al];
+        st.dir[al][0] = st.dir[al][1] = st.dir[al][2] = 0;
+        st.dir[al][al] = 1;
+        st.coef[al] = c / (mt.dxi[al] * mt.dxi[al]);
+    }
+    for (int p = 0; p < n_aux; ++p) {
+        for (int k = 0; k < 3; ++k) {
+            st.dir[3 + p][k] = aux[p][k];
+            st.a[p][k] = a[p][k];
+        }
+        st.b[p] = b[p];
+        st.coef[3 + p] = b[p] / (len[p] * len[p]);
+    }
+    if (!negative_definite(st, fd_n)) return EXX_ERR_NK;
+    return EXX_OK;
+}
+
+int make_offsets(const Metric &mt, double r_pe, double r_me, OffsetSet &o)
+{
+    o = OffsetSet();
+    if (!(r_pe > 0.0) || !(r_me >= r_pe)) return EXX_ERR_ARG;
+    int H[3];
+    for (int al = 0; al < 3; ++al) {
+        const double rn = std::sqrt(mt.hinv[al][0] * mt.hinv[al][0] + mt.hinv[al][1] * mt.hinv[al][1] +
+                                    mt.hinv[al][2] * mt.hinv[al][2]);
+        H[al] = (int)std::ceil(r_me * mt.n[al] * rn);
+        if (H[al] > 500) return EXX_ERR_ARG;
+    }
+    const double pe2 = r_pe * r_pe, me2 = r_me * r_me;
+    std::vector<int> shell;
+    for (int i = -H[0]; i <= H[0]; ++i)
+        for (int j = -H[1]; j <= H[1]; ++j)
+            for (int k = -H[2]; k <= H[2]; ++k) {
+                const int m[3] = {i, j, k};
+                double r[3];
+                step_vec(mt, m, r);
+                const double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                if (d2 <= pe2) {
+                    o.m.insert(o.m.end(), m, m + 3);
+                } else if (d2 <= me2) {
+                    shell.insert(shell.end(), m, m + 3);
+                }
+            }
+    o.n_pe = (int)(o.m.size() / 3);
+    o.m.insert(o.m.end(), shell.begin(), shell.end());
+    o.n_me = (int)(o.m.size() / 3);
+    return EXX_OK;
+}
+
+int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L)
+{
+    L = SetLayout();
+    int Hpe[3] = {0, 0, 0}, Hme[3] = {0, 0, 0};
+    for (int q = 0; q < o.n_me; ++q)
+        for (int al = 0; al < 3; ++al) {
+            const int v = std::abs(o.m[3 * q + al]);
+            Hme[al] = std::max(Hme[al], v);
+            if (q < o.n_pe) Hpe[al] = std::max(Hpe[al], v);
+        }
+    int reach[3];
+    for (int al = 0; al < 3; ++al) {
+        int r = 1;
+        for (int d = 0; d < st.ndir; ++d) r = std::max(r, std::abs(st.dir[d][al]));
+        reach[al] = fd_n * r;
+    }
+    for (int al = 0; al < 3; ++al) {
+        L.c[al] = Hpe[al] + reach[al];
+        L.B[al] = 2 * L.c[al] + 1;
+    }
+    L.box = (long long)L.B[0] * L.B[1] * L.B[2];
+    if (L.box > (1LL << 30)) return EXX_ERR_ARG;
+    for (int d = 0; d < st.ndir; ++d) L.dstride[d] = (st.dir[d][0] * L.B[1] + st.dir[d][1]) * L.B[2] + st.dir[d][2];
+    L.gstride[0] = L.B[1] * L.B[2];
+    L.gstride[1] = L.B[2];
+    L.gstride[2] = 1;
+    // membership map over the ME bounding box: 1 PE, 2 shell
+    const int MB[3] = {2 * Hme[0] + 1, 2 * Hme[1] + 1, 2 * Hme[2] + 1};
+    std::vector<int> memb((size_t)MB[0] * MB[1] * MB[2], 0), shell_idx((size_t)MB[0] * MB[1] * MB[2], -1);
+    auto mindex = [&](int m0, int m1, int m2) -> long long {
+        if (std::abs(m0) > Hme[0] || std::abs(m1) > Hme[1] || std::abs(m2) > Hme[2]) return -1;
+        return ((long long)(m0 + Hme[0]) * MB[1] + (m1 + Hme[1])) * MB[2] + (m2 + Hme[2]);
+    };
+    for (int q = 0; q < o.n_me; ++q) {
+        const long long id = mindex(o.m[3 * q], o.m[3 * q + 1], o.m[3 * q + 2]);
+        memb[id] = q < o.n_pe ? 1 : 2;
+        if (q >= o.n_pe) shell_idx[id] = q - o.n_pe;
+    }
+    const int n_shell = o.n_me - o.n_pe;
+    std::vector<char> is_halo(n_shell, 0);
+    for (int q = 0; q < o.n_pe; ++q) {
+        const int *m = &o.m[3 * q];
+        for (int d = 0; d < st.ndir; ++d)
+            for (int s = -fd_n; s <= fd_n; ++s) {
+                if (!s) continue;
+                const long long id = mindex(m[0] + s * st.dir[d][0], m[1] + s * st.dir[d][1], m[2] + s * st.dir[d][2]);
+                if (id < 0 || memb[id] == 0) return EXX_ERR_HALO;
+                if (memb[id] == 2) is_halo[shell_idx[id]] = 1;
+            }
+    }
+    auto box_off = [&](const int *m) -> int32_t {
+        return (int32_t)(((long long)(m[0] + L.c[0]) * L.B[1] + (m[1] + L.c[1])) * L.B[2] + (m[2] + L.c[2]));
+    };
+    L.n_pe = o.n_pe;
+    L.n_shell = n_shell;
+    L.pe_m.resize(o.n_pe);
+    L.pe_off.resize(o.n_pe);
+    for (int q = 0; q < o.n_pe; ++q) {
+        const int *m = &o.m[3 * q];
+        L.pe_m[q] = pack_m(m[0], m[1], m[2]);
+        L.pe_off[q] = box_off(m);
+    }
+    L.sh_m.reserve(n_shell);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int s = 0; s < n_shell; ++s) {
+            if ((pass == 0) != (is_halo[s] != 0)) continue;
+            const int *m = &o.m[3 * (o.n_pe + s)];
+            L.sh_m.push_back(pack_m(m[0], m[1], m[2]));
+            if (pass == 0) L.halo_off.push_back(box_off(m));
+        }
+    L.n_halo = (int)L.halo_off.size();
+    return EXX_OK;
+}
+
+}  // namespace exx

@@ -1,0 +1,73 @@
+// plan.h -- host-side geometry of the EXX pair path (cell metric, Natan-Kronik
+// stencil, proto-subdomain offset sets and the dense CG box layout).
+//
+// Everything here is computed once per cell (or per MD step for a fluctuating
+// cell) on the host and uploaded as small constant tables; the per-pair work
+// runs in the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace exx {
+
+constexpr int kMaxFd = 6;     // largest stencil half-width n
+constexpr int kMaxL = 6;      // largest multipole order
+constexpr int kNlmMax = (kMaxL + 1) * (kMaxL + 1);
+
+// Cell tensor and the quantities of Sec. II B 1 and Eqs. jacb, lapG_.
+struct Metric {
+    double h[3][3];       // h[a][alpha] = (L_alpha)_a
+    double hinv[3][3];    // adjugate / det, fixed operation order (pair-list bit-exactness)
+    double J[3][3];       // J[a][alpha] = |L_alpha| hinv[alpha][a]
+    double F[3][3];       // F = J^T J
+    double vol, dv;
+    double len[3], dxi[3];
+    int n[3];
+};
+int make_metric(const double lattice[3][3], const int n[3], Metric &m);
+
+// Pure-derivative directions of the NK Laplacian (Eq. lapG_mod_nk3d): the three
+// lattice axes and n_aux auxiliary grid directions.
+struct Stencil {
+    int n_off = 0, n_aux = 0, ndir = 3;
+    int dir[6][3] = {};
+    double coef[6] = {};      // multiplies sum_q w_q f(g + q dir); includes 1/step^2
+    double b[3] = {};
+    double a[3][3] = {};
+};
+// aux == nullptr: choose the directions (2D bisector rule or Algorithm 1).
+int make_stencil(const Metric &m, int fd_n, int nq, const int (*aux)[3], int n_aux_fixed, Stencil &st);
+
+// Central-difference weights w2[0..n] (second derivative, Eq. d2_1) and
+// w1[0..n] (first derivative, Eq. d1_1), from the moment conditions.
+void fd_weights(int n, double *w2, double *w1);
+
+// Integer offsets m of the proto-subdomains (Eqs. rbar, g0): PE points
+// |h m/N| <= R_PE first, then the shell R_PE < |h m/N| <= R_ME, lexicographic.
+struct OffsetSet {
+    std::vector<int> m;   // [n_me][3]
+    int n_pe = 0, n_me = 0;
+};
+int make_offsets(const Metric &mt, double r_pe, double r_me, OffsetSet &o);
+
+// Dense CG box and the per-point index tables uploaded to the device.
+//   box: PE bounding box plus the stencil reach on every side; element of
+//   offset m sits at ((m0 + c0) B1 + (m1 + c1)) B2 + (m2 + c2).
+//   shell points are reordered: halo (reached by a stencil from PE) first.
+struct SetLayout {
+    int n_pe = 0, n_shell = 0, n_halo = 0;
+    int B[3] = {}, c[3] = {};
+    long long box = 0;
+    int dstride[6] = {};
+    int gstride[3] = {};
+    std::vector<int32_t> pe_m, pe_off;     // packed offsets and box offsets of PE points
+    std::vector<int32_t> sh_m, halo_off;   // packed offsets of shell points; box offsets of halo points
+};
+int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
+
+// Packing of an offset triple with |m_alpha| <= 511 into one int32.
+inline int32_t pack_m(int m0, int m1, int m2) {
+    return (int32_t)(((uint32_t)(m0 + 512) << 20) | ((uint32_t)(m1 + 512) << 10) | (uint32_t)(m2 + 512));
+}
+
+}  // namespace exx
