@@ -199,6 +199,10 @@ int exx_ctx_get_timing(const exx_ctx *ctx, double ms[4]);
 
 const char *exx_error_string(int code);
 
+/* The CUDA call and error behind the calling thread's last EXX_ERR_CUDA
+ * ("" if none); valid until the next failing call on this thread. */
+const char *exx_last_error_detail(void);
+
 /* Library version string. */
 const char *exx_version(void);
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -17,10 +18,20 @@
 
 using namespace exx;
 
-#define CK(call)                                     \
-    do {                                             \
-        cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return EXX_ERR_CUDA;  \
+namespace {
+thread_local char g_err_detail[256] = "";
+int cuda_fail(cudaError_t e, int line)
+{
+    std::snprintf(g_err_detail, sizeof(g_err_detail), "api.cu:%d: %s (%s)", line, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return EXX_ERR_CUDA;
+}
+}  // namespace
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, __LINE__); \
     } while (0)
 
 namespace {
@@ -75,6 +86,7 @@ struct exx_ctx {
 
 struct exx_plan {
     exx_ctx *ctx = nullptr;
+    int device = 0;
     exx_cell cell0{};      // cell the offsets / aux directions were built for
     exx_cell cell{};       // cell of the last metric update
     exx_params params{};
@@ -352,6 +364,8 @@ extern "C" {
 
 const char *exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
 
+const char *exx_last_error_detail(void) { return g_err_detail; }
+
 const char *exx_error_string(int code)
 {
     switch (code) {
@@ -441,6 +455,7 @@ int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params
     exx_plan *p = new (std::nothrow) exx_plan();
     if (!p) return EXX_ERR_OOM;
     p->ctx = ctx;
+    p->device = ctx->device;
     p->cell0 = *cell;
     p->params = *params;
     p->max_orb = max_orb;
@@ -464,7 +479,7 @@ int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params
 void exx_plan_destroy(exx_plan *p)
 {
     if (!p) return;
-    cudaSetDevice(p->ctx->device);
+    cudaSetDevice(p->device);
     free_geometry(p);
     dev_free(p->d_phi);
     dev_free(p->d_centres);
@@ -529,7 +544,7 @@ int exx_get_pair_list(exx_plan *p, int cap, int *n, int *rows)
     if (p->last_count == 0) return EXX_OK;
     if (!rows) return EXX_ERR_ARG;
     std::vector<PairRec> h(p->last_count);
-    CK(cudaSetDevice(p->ctx->device));
+    CK(cudaSetDevice(p->device));
     CK(cudaMemcpy(h.data(), p->d_pairs, sizeof(PairRec) * p->last_count, cudaMemcpyDeviceToHost));
     for (int t = 0; t < p->last_count; ++t) {
         int *r = rows + 8 * (size_t)t;
@@ -550,6 +565,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     if (n_cells > 64) return EXX_ERR_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     CK(cudaSetDevice(ctx->device));
+    cudaGetLastError();   // clear a stale non-sticky error of an earlier unrelated call
     const int prec = plans[0]->params.precision;
     for (int c = 0; c < n_cells; ++c) {
         exx_plan *p = plans[c];

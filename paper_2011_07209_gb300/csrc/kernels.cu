@@ -565,72 +565,166 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *
                 rnorm = sqrt(rr);
             }
         } else {
-            // mixed: FP32 CG on the correction inside an FP64-residual refinement loop
-            float *pf = (float *)pbox;
-            float *rf = (float *)rv;
-            float *qf = (float *)qv;
-            float *ef = (float *)ev;
-            while (bn > 0.0 && rnorm > stop) {
-                if (iters >= C.max_iter) {
-                    status = 5;
-                    break;
-                }
-                double rr0[1] = {0.0};
+            // Mixed: FP32 CG with reliable updates.  The FP32 vectors live in a frame
+            // scaled by S (the true residual norm at the last update), so they stay O(1)
+            // however small the pair density is.  The FP32 correction e accumulates
+            // alpha p; when the recursive residual has dropped by inner_red since the
+            // last update (or reaches the target), x += S e in FP64, the true residual
+            // b - A x is recomputed in FP64 and replaces r, and the search direction is
+            // carried over into the new frame.
+            float *__restrict__ pf = (float *)pbox;
+            float *__restrict__ rf = (float *)rv;
+            float *__restrict__ qf = (float *)qv;
+            float *__restrict__ ef = (float *)ev;
+            const int32_t *__restrict__ poff = S.pe_off;
+            const int npe = S.n_pe;
+            constexpr int U = 4;
+            if (bn > 0.0) {
+                double S_ = bn;
+                double rr;
                 {
+                    double a0[1];
                     DF a = {0.f, 0.f};
-                    for (int k = tid; k < S.n_pe; k += nt) {
-                        const float r = (float)r64[k];
+                    const double sc = 1.0 / S_;
+                    for (int k = tid; k < npe; k += nt) {
+                        const float r = (float)(r64[k] * sc);
                         rf[k] = r;
                         ef[k] = 0.f;
-                        pf[S.pe_off[k]] = r;
+                        pf[poff[k]] = r;
                         df_fma(a, r, r);
                     }
-                    rr0[0] = df_val(a);
+                    a0[0] = df_val(a);
+                    block_sum<1>(a0, red);
+                    rr = a0[0];
                 }
-                block_sum<1>(rr0, red);
-                double rr = rr0[0];
-                const double inner_stop = fmax(inner_red * sqrt(rr), 0.5 * stop);
+                double rmax = sqrt(rr);
                 for (;;) {
+                    if (iters >= C.max_iter) {
+                        status = 5;
+                        break;
+                    }
+                    // pass A: q = A p, <p, q>
                     double pq[1];
                     {
                         DF a = {0.f, 0.f};
-                        for (int k = tid; k < S.n_pe; k += nt) {
-                            const int off = S.pe_off[k];
-                            const float q = -lap_at<float>(pf, off, sm.cw32, sm.ds, ndir, fdn, sm.center32);
-                            qf[k] = q;
-                            df_fma(a, pf[off], q);
+                        for (int kb = tid; kb < npe; kb += U * nt) {
+                            int off[U];
+                            float q[U], pc[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                off[u] = k < npe ? __ldg(poff + k) : -1;
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (off[u] >= 0) {
+                                    pc[u] = pf[off[u]];
+                                    q[u] = -lap_at<float>(pf, off[u], sm.cw32, sm.ds, ndir, fdn, sm.center32);
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (off[u] >= 0) {
+                                    qf[kb + u * nt] = q[u];
+                                    df_fma(a, pc[u], q[u]);
+                                }
+                            }
                         }
                         pq[0] = df_val(a);
                     }
                     block_sum<1>(pq, red);
                     const float alpha = (float)(rr / pq[0]);
+                    // pass B: r -= alpha q, <r, r>
                     double rn[1];
                     {
                         DF a = {0.f, 0.f};
-                        for (int k = tid; k < S.n_pe; k += nt) {
-                            const int off = S.pe_off[k];
-                            ef[k] += alpha * pf[off];
-                            const float r = rf[k] - alpha * qf[k];
-                            rf[k] = r;
-                            df_fma(a, r, r);
+                        for (int kb = tid; kb < npe; kb += U * nt) {
+                            float rv_[U], qv_[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                if (k < npe) {
+                                    rv_[u] = rf[k];
+                                    qv_[u] = qf[k];
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                if (k < npe) {
+                                    const float r = rv_[u] - alpha * qv_[u];
+                                    rf[k] = r;
+                                    df_fma(a, r, r);
+                                }
+                            }
                         }
                         rn[0] = df_val(a);
                     }
                     block_sum<1>(rn, red);
                     ++iters;
-                    if (sqrt(rn[0]) <= inner_stop || iters >= C.max_iter) break;
+                    const double rnrm = sqrt(rn[0]);
+                    if (rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop || !(rnrm == rnrm)) {
+                        // reliable update in FP64: x += S (e + alpha p)
+                        for (int k = tid; k < npe; k += nt) {
+                            const int off = poff[k];
+                            vbox[off] += ((double)ef[k] + (double)alpha * (double)pf[off]) * S_;
+                            ef[k] = 0.f;
+                        }
+                        __syncthreads();
+                        rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+                        ++refine;
+                        if (rnorm <= stop) break;
+                        // beta from the replaced residual, direction moved to the new frame
+                        const double Snew = rnorm;
+                        const float bscaled = (float)((rnorm / S_) * (rnorm / S_) / rr * (S_ / Snew));
+                        const double sc = 1.0 / Snew;
+                        double a0[1];
+                        DF a = {0.f, 0.f};
+                        for (int k = tid; k < npe; k += nt) {
+                            const int off = poff[k];
+                            const float r = (float)(r64[k] * sc);
+                            rf[k] = r;
+                            pf[off] = r + bscaled * pf[off];
+                            df_fma(a, r, r);
+                        }
+                        a0[0] = df_val(a);
+                        block_sum<1>(a0, red);
+                        rr = a0[0];
+                        rmax = sqrt(rr);
+                        S_ = Snew;
+                        continue;
+                    }
+                    // pass C: e += alpha p, p = r + beta p
                     const float beta = (float)(rn[0] / rr);
                     rr = rn[0];
-                    for (int k = tid; k < S.n_pe; k += nt) {
-                        const int off = S.pe_off[k];
-                        pf[off] = rf[k] + beta * pf[off];
+                    for (int kb = tid; kb < npe; kb += U * nt) {
+                        int off[U];
+                        float pv_[U], rv_[U], ev_[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            off[u] = k < npe ? __ldg(poff + k) : -1;
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            if (off[u] >= 0) {
+                                pv_[u] = pf[off[u]];
+                                rv_[u] = rf[k];
+                                ev_[u] = ef[k];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            if (off[u] >= 0) {
+                                ef[k] = ev_[u] + alpha * pv_[u];
+                                pf[off[u]] = rv_[u] + beta * pv_[u];
+                            }
+                        }
                     }
                     __syncthreads();
                 }
-                for (int k = tid; k < S.n_pe; k += nt) vbox[S.pe_off[k]] += (double)ef[k];
-                __syncthreads();
-                rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
-                ++refine;
             }
         }
 

@@ -7,7 +7,7 @@
 namespace exx {
 
 constexpr int kRowThreads = 128;     // pair-list CTA size
-constexpr int kSolveThreads = 512;   // persistent pair-solver CTA size
+constexpr int kSolveThreads = 1024;  // persistent pair-solver CTA size
 
 // Per-CTA scratch of the persistent solver: one slot per CTA, all slots equal.
 struct SolveSlots {

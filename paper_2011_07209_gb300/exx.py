@@ -25,7 +25,7 @@ _lock = threading.Lock()
 
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
-           "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_version")
+           "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version")
 
 
 class Cell(C.Structure):
@@ -64,6 +64,8 @@ class PlanInfo(C.Structure):
 class ExxError(RuntimeError):
     def __init__(self, code, where=""):
         msg = lib().exx_error_string(code).decode() if _lib is not None else str(code)
+        if code == ERR_CUDA and _lib is not None:
+            msg += " [" + lib().exx_last_error_detail().decode() + "]"
         super().__init__(f"{where}: {msg} (code {code})")
         self.code = code
 
@@ -85,6 +87,7 @@ def lib(build_if_missing: bool = False):
             L = C.CDLL(path)
             L.exx_error_string.restype = C.c_char_p
             L.exx_version.restype = C.c_char_p
+            L.exx_last_error_detail.restype = C.c_char_p
             L.exx_ctx_create.argtypes = [C.POINTER(C.c_void_p), C.c_int]
             L.exx_ctx_destroy.argtypes = [C.c_void_p]
             L.exx_ctx_destroy.restype = None
@@ -157,7 +160,9 @@ def dbox_layout(lattice, n, centres, params: Params):
 
 class Context:
     def __init__(self, device: int = 0):
+        import weakref
         self.handle = C.c_void_p()
+        self._plans = weakref.WeakSet()
         _check(lib().exx_ctx_create(C.byref(self.handle), int(device)), "exx_ctx_create")
 
     def set_timing(self, enable: bool = True):
@@ -169,7 +174,10 @@ class Context:
         return {"tables_ms": ms[0], "pairlist_ms": ms[1], "solve_ms": ms[2], "finalize_ms": ms[3]}
 
     def close(self):
+        """Destroy the context; plans made from it are closed first."""
         if self.handle:
+            for p in list(self._plans):
+                p.close()
             lib().exx_ctx_destroy(self.handle)
             self.handle = C.c_void_p()
 
@@ -188,6 +196,7 @@ class Plan:
         bx = (C.c_int * 3)(*[int(b) for b in box])
         _check(lib().exx_plan_create(ctx.handle, C.byref(make_cell(lattice, n)), C.byref(params), int(max_orb), bx,
                                      C.byref(self.handle)), "exx_plan_create")
+        ctx._plans.add(self)
 
     def info(self) -> dict:
         pi = PlanInfo()
