@@ -78,7 +78,7 @@ struct exx_ctx {
     CellDev *h_cells = nullptr;       // pinned
     CellResult *h_res = nullptr;      // pinned
     int cells_cap = 0;
-    int inner_shift = 14;
+    int inner_shift = 10;
     bool timing = false;
     cudaEvent_t ev[5] = {};
     double ms[4] = {};
@@ -96,7 +96,7 @@ struct exx_plan {
     int n_aux = 0;
     OffsetSet off[2];
     SetLayout lay[2];
-    int32_t *d_pe_m[2] = {}, *d_pe_off[2] = {}, *d_sh_m[2] = {}, *d_halo_off[2] = {};
+    int32_t *d_pe_m[2] = {}, *d_pe_off[2] = {}, *d_sh_m[2] = {}, *d_halo_off[2] = {}, *d_groups[2] = {};
     double *d_S64[2] = {}, *d_T64[2] = {};
     float *d_S32[2] = {}, *d_T32[2] = {};
     bool tables_valid = false;
@@ -138,6 +138,7 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_pe_off[s]);
         dev_free(p->d_sh_m[s]);
         dev_free(p->d_halo_off[s]);
+        dev_free(p->d_groups[s]);
         dev_free(p->d_S64[s]);
         dev_free(p->d_T64[s]);
         dev_free(p->d_S32[s]);
@@ -167,6 +168,7 @@ static int build_geometry(exx_plan *p)
         const SetLayout &L = p->lay[s];
         if ((e = dev_alloc(&p->d_pe_m[s], L.n_pe)) || (e = dev_alloc(&p->d_pe_off[s], L.n_pe)) ||
             (e = dev_alloc(&p->d_sh_m[s], L.n_shell)) || (e = dev_alloc(&p->d_halo_off[s], L.n_halo)) ||
+            (e = dev_alloc(&p->d_groups[s], L.groups.size())) ||
             (e = dev_alloc(&p->d_S64[s], (size_t)L.n_pe * kNlm)) ||
             (e = dev_alloc(&p->d_S32[s], (size_t)L.n_pe * kNlm)) ||
             (e = dev_alloc(&p->d_T64[s], (size_t)L.n_shell * kNlm)) ||
@@ -176,6 +178,8 @@ static int build_geometry(exx_plan *p)
         CK(cudaMemcpy(p->d_pe_off[s], L.pe_off.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
         if (L.n_shell) CK(cudaMemcpy(p->d_sh_m[s], L.sh_m.data(), 4 * L.n_shell, cudaMemcpyHostToDevice));
         if (L.n_halo) CK(cudaMemcpy(p->d_halo_off[s], L.halo_off.data(), 4 * L.n_halo, cudaMemcpyHostToDevice));
+        if (!L.groups.empty())
+            CK(cudaMemcpy(p->d_groups[s], L.groups.data(), 4 * L.groups.size(), cudaMemcpyHostToDevice));
     }
     p->cell = p->cell0;
     p->tables_valid = false;
@@ -255,6 +259,12 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
         S.pe_off = p->d_pe_off[s];
         S.sh_m = p->d_sh_m[s];
         S.halo_off = p->d_halo_off[s];
+        S.groups = p->d_groups[s];
+        S.n_groups = (int)L.groups.size();
+        for (int d = 0; d < 6; ++d) {
+            S.rstride[d] = L.rstride[d];
+            S.d2[d] = d < p->stencil.ndir ? p->stencil.dir[d][2] : 0;
+        }
         S.S64 = p->d_S64[s];
         S.S32 = p->d_S32[s];
         S.T64 = p->d_T64[s];
@@ -316,22 +326,26 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
     const int bpm = std::max(1, solve_blocks_per_sm(mixed));
     const int n_slots = bpm * c->n_sm;
     // one layout that serves both precisions: boxes and vectors sized for doubles
+    // every array sits 128 bytes past a 256-byte boundary with 128 bytes of
+    // padding after it, so aligned 16-byte group loads one group beyond either
+    // end of a box stay inside the slot
     SolveSlots s{};
     size_t o = 0;
-    s.off_vbox = o;
-    o += align256(8 * box_max);
-    s.off_pbox = o;
-    o += align256(8 * box_max);
-    s.off_rho = o;
-    o += align256(8 * npe_max);
-    s.off_r64 = o;
-    o += align256(8 * npe_max);
-    s.off_r = o;
-    o += align256(8 * npe_max);
-    s.off_q = o;
-    o += align256(8 * npe_max);
-    s.off_e = o;
-    o += align256(8 * npe_max);
+    const size_t boxb = align256(8 * box_max + 256), vecb = align256(8 * std::max(npe_max, box_max) + 256);
+    s.off_vbox = o + 128;
+    o += boxb;
+    s.off_pbox = o + 128;
+    o += boxb;
+    s.off_rho = o + 128;
+    o += align256(8 * npe_max + 256);
+    s.off_r64 = o + 128;
+    o += align256(8 * npe_max + 256);
+    s.off_r = o + 128;
+    o += vecb;
+    s.off_q = o + 128;
+    o += vecb;
+    s.off_e = o + 128;
+    o += vecb;
     s.slot_bytes = o;
     s.n_slots = n_slots;
     const size_t need = s.slot_bytes * (size_t)n_slots;

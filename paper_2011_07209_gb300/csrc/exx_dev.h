@@ -17,6 +17,10 @@ struct SetDev {
     const int32_t *pe_off;         // [n_pe] dense-box offsets
     const int32_t *sh_m;           // [n_shell] packed offsets, halo points first
     const int32_t *halo_off;       // [n_halo] dense-box offsets
+    const int32_t *groups;         // [n_groups] aligned 4-point groups: (offset/4) << 4 | PE mask
+    int n_groups;
+    int rstride[6];                // dstride without the last-axis component
+    int d2[6];                     // last-axis component of each direction
     const double *S64;             // [n_pe][kNlm] regular solid harmonics r^l Y_lm(r-bar)
     const float *S32;
     const double *T64;             // [kNlm][n_shell] 4 pi / (2l+1) r^l Y_lm / r^(2l+1)

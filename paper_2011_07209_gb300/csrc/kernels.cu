@@ -17,6 +17,10 @@
 
 namespace exx {
 
+#ifndef EXX_UNROLL
+#define EXX_UNROLL 4
+#endif
+
 constexpr double kFourPi = 12.566370614359172953850573533118;
 
 __device__ __forceinline__ void unpack_m(int32_t p, int &m0, int &m1, int &m2)
@@ -387,6 +391,396 @@ struct SmemCell {
     int ds[6];
 };
 
+// The mixed-precision Poisson solve of one pair (see the comment inside).
+struct CgMixed {
+    const SetDev *S;
+    double *vbox;
+    const double *rho;
+    double *r64;
+    float *pf, *rf, *qf, *ef;
+    const SmemCell *sm;
+    double *red;
+    int ndir, fdn, max_iter;
+    double stop, bn, inner_red;
+};
+
+__device__ __noinline__ void cg_mixed(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
+{
+    const SetDev &S = *cg.S;
+    const SmemCell &sm = *cg.sm;
+    double *__restrict__ vbox = cg.vbox;
+    const double *__restrict__ rho = cg.rho;
+    double *__restrict__ r64 = cg.r64;
+    double *red = cg.red;
+    const int ndir = cg.ndir, fdn = cg.fdn;
+    const double stop = cg.stop, bn = cg.bn, inner_red = cg.inner_red;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    struct {
+        int max_iter;
+    } C = {cg.max_iter};
+            // Mixed: FP32 CG with reliable updates.  The FP32 vectors live in a frame
+            // scaled by S (the true residual norm at the last update), so they stay O(1)
+            // however small the pair density is.  The FP32 correction e accumulates
+            // alpha p; when the recursive residual has dropped by inner_red since the
+            // last update (or reaches the target), x += S e in FP64, the true residual
+            // b - A x is recomputed in FP64 and replaces r, and the search direction is
+            // carried over into the new frame.
+            float *__restrict__ pf = cg.pf;
+            float *__restrict__ rf = cg.rf;
+            float *__restrict__ qf = cg.qf;
+            float *__restrict__ ef = cg.ef;
+            const int32_t *__restrict__ poff = S.pe_off;
+            const int npe = S.n_pe;
+            constexpr int U = EXX_UNROLL;
+            if (bn > 0.0) {
+                double S_ = bn;
+                double rr;
+                {
+                    double a0[1];
+                    DF a = {0.f, 0.f};
+                    const double sc = 1.0 / S_;
+                    for (int k = tid; k < npe; k += nt) {
+                        const float r = (float)(r64[k] * sc);
+                        rf[k] = r;
+                        ef[k] = 0.f;
+                        pf[poff[k]] = r;
+                        df_fma(a, r, r);
+                    }
+                    a0[0] = df_val(a);
+                    block_sum<1>(a0, red);
+                    rr = a0[0];
+                }
+                double rmax = sqrt(rr);
+                for (;;) {
+                    if (iters >= C.max_iter) {
+                        status = 5;
+                        break;
+                    }
+                    // pass A: q = A p, <p, q>
+                    double pq[1];
+                    {
+                        DF a = {0.f, 0.f};
+                        for (int kb = tid; kb < npe; kb += U * nt) {
+                            int off[U];
+                            float q[U], pc[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                off[u] = k < npe ? __ldg(poff + k) : -1;
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (off[u] >= 0) {
+                                    pc[u] = pf[off[u]];
+                                    q[u] = -lap_at<float>(pf, off[u], sm.cw32, sm.ds, ndir, fdn, sm.center32);
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (off[u] >= 0) {
+                                    qf[kb + u * nt] = q[u];
+                                    df_fma(a, pc[u], q[u]);
+                                }
+                            }
+                        }
+                        pq[0] = df_val(a);
+                    }
+                    block_sum<1>(pq, red);
+                    const float alpha = (float)(rr / pq[0]);
+                    // pass B: r -= alpha q, <r, r>
+                    double rn[1];
+                    {
+                        DF a = {0.f, 0.f};
+                        for (int kb = tid; kb < npe; kb += U * nt) {
+                            float rv_[U], qv_[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                if (k < npe) {
+                                    rv_[u] = rf[k];
+                                    qv_[u] = qf[k];
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int k = kb + u * nt;
+                                if (k < npe) {
+                                    const float r = rv_[u] - alpha * qv_[u];
+                                    rf[k] = r;
+                                    df_fma(a, r, r);
+                                }
+                            }
+                        }
+                        rn[0] = df_val(a);
+                    }
+                    block_sum<1>(rn, red);
+                    ++iters;
+                    const double rnrm = sqrt(rn[0]);
+                    if (rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop || !(rnrm == rnrm)) {
+                        // reliable update in FP64: x += S (e + alpha p)
+                        for (int k = tid; k < npe; k += nt) {
+                            const int off = poff[k];
+                            vbox[off] += ((double)ef[k] + (double)alpha * (double)pf[off]) * S_;
+                            ef[k] = 0.f;
+                        }
+                        __syncthreads();
+                        rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+                        ++refine;
+                        if (rnorm <= stop) break;
+                        // beta from the replaced residual, direction moved to the new frame
+                        const double Snew = rnorm;
+                        const float bscaled = (float)((rnorm / S_) * (rnorm / S_) / rr * (S_ / Snew));
+                        const double sc = 1.0 / Snew;
+                        double a0[1];
+                        DF a = {0.f, 0.f};
+                        for (int k = tid; k < npe; k += nt) {
+                            const int off = poff[k];
+                            const float r = (float)(r64[k] * sc);
+                            rf[k] = r;
+                            pf[off] = r + bscaled * pf[off];
+                            df_fma(a, r, r);
+                        }
+                        a0[0] = df_val(a);
+                        block_sum<1>(a0, red);
+                        rr = a0[0];
+                        rmax = sqrt(rr);
+                        S_ = Snew;
+                        continue;
+                    }
+                    // pass C: e += alpha p, p = r + beta p
+                    const float beta = (float)(rn[0] / rr);
+                    rr = rn[0];
+                    for (int kb = tid; kb < npe; kb += U * nt) {
+                        int off[U];
+                        float pv_[U], rv_[U], ev_[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            off[u] = k < npe ? __ldg(poff + k) : -1;
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            if (off[u] >= 0) {
+                                pv_[u] = pf[off[u]];
+                                rv_[u] = rf[k];
+                                ev_[u] = ef[k];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int k = kb + u * nt;
+                            if (off[u] >= 0) {
+                                ef[k] = ev_[u] + alpha * pv_[u];
+                                pf[off[u]] = rv_[u] + beta * pv_[u];
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+}
+
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+
+// Mixed-precision Poisson solve of one pair on aligned 4-point groups.
+//
+// Same algorithm as cg_mixed (FP32 CG in a frame scaled by the last true
+// residual norm, FP64 reliable updates), restructured for bandwidth:
+//   * every FP32 vector (p, r, q, e) is a dense box, zero outside PE, and the
+//     passes walk the list of aligned 4-point groups with 16-byte accesses;
+//   * the stencil reads p with aligned float4 loads for the directions that do
+//     not step along the last axis, a 12-wide register window for the last
+//     axis, and scalar loads for auxiliary directions with a last-axis step;
+//   * one reduction per iteration: pass A forms q = A p together with <p,q>,
+//     <q,q>, <r,q> and <r,p>; then alpha = <r,p>/<p,q> (exact line search),
+//     <r',r'> = <r,r> - 2 alpha <r,q> + alpha^2 <q,q>, and the Hestenes-Stiefel
+//     beta = -(<r,q> - alpha <q,q>) / <p,q> keeps p' A-conjugate to p, so r, e
+//     and p are updated in one fused pass.  These forms stay exact when an FP64
+//     residual replacement has perturbed the Krylov relations; after a
+//     replacement the new direction is r' + gamma p with gamma chosen to keep
+//     it A-conjugate to the last direction.
+template <int FDN>
+__device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
+{
+    const SetDev &S = *cg.S;
+    const SmemCell &sm = *cg.sm;
+    double *__restrict__ vbox = cg.vbox;
+    const double *__restrict__ rho = cg.rho;
+    double *__restrict__ r64 = cg.r64;
+    float *__restrict__ pf = cg.pf;
+    float *__restrict__ rf = cg.rf;
+    float *__restrict__ qf = cg.qf;
+    float *__restrict__ ef = cg.ef;
+    const int32_t *__restrict__ poff = S.pe_off;
+    const int32_t *__restrict__ grp = S.groups;
+    double *red = cg.red;
+    const int npe = S.n_pe, ng = S.n_groups;
+    const int ndir = cg.ndir, fdn = cg.fdn;
+    const double stop = cg.stop, inner_red = cg.inner_red;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (!(cg.bn > 0.0)) return;
+
+    // coefficients and strides are read from shared memory (broadcast) to keep
+    // the register budget of 1024-thread CTAs
+    const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
+    const float(*cw)[8] = sm.cw32;
+    const float center = sm.center32;
+
+    double S_ = cg.bn;
+    double rr;
+    {
+        double a0[1];
+        DF a = {0.f, 0.f};
+        const double sc = 1.0 / S_;
+        for (int k = tid; k < npe; k += nt) {
+            const int off = poff[k];
+            const float r = (float)(r64[k] * sc);
+            rf[off] = r;
+            ef[off] = 0.f;
+            pf[off] = r;
+            df_fma(a, r, r);
+        }
+        a0[0] = df_val(a);
+        block_sum<1>(a0, red);
+        rr = a0[0];
+    }
+    double rmax = sqrt(rr);
+    for (;;) {
+        if (iters >= cg.max_iter) {
+            status = 5;
+            break;
+        }
+        // ---- pass A: q = A p on every group, <p,q>, <q,q>, <r,q> ----
+        double dots[4];
+        {
+            DF apq = {0.f, 0.f}, aqq = {0.f, 0.f}, arq = {0.f, 0.f}, arp = {0.f, 0.f};
+            for (int g = tid; g < ng; g += nt) {
+                const int32_t gw = __ldg(grp + g);
+                const int off = (gw >> 4) << 2;
+                const int mask = gw & 15;
+                const float4 c = ld4(pf + off);
+                const float4 cm = ld4(pf + off - 4);
+                const float4 cp = ld4(pf + off + 4);
+                const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
+                float acc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
+#pragma unroll
+                for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    if (d == 2 || d >= ndir) continue;
+                    if (d2[d] == 0) {
+#pragma unroll
+                        for (int s_ = 1; s_ <= FDN; ++s_) {
+                            const float4 a = ld4(pf + off + s_ * rs[d]);
+                            const float4 b = ld4(pf + off - s_ * rs[d]);
+                            acc[0] += cw[d][s_] * (a.x + b.x);
+                            acc[1] += cw[d][s_] * (a.y + b.y);
+                            acc[2] += cw[d][s_] * (a.z + b.z);
+                            acc[3] += cw[d][s_] * (a.w + b.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                acc[i] += cw[d][s_] * (pf[off + i + s_ * dsf[d]] + pf[off + i - s_ * dsf[d]]);
+                    }
+                }
+                const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
+                const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
+                st4(qf + off, q0, q1, q2, q3);
+                const float4 r = ld4(rf + off);
+                df_fma(apq, c.x, q0);
+                df_fma(apq, c.y, q1);
+                df_fma(apq, c.z, q2);
+                df_fma(apq, c.w, q3);
+                df_fma(aqq, q0, q0);
+                df_fma(aqq, q1, q1);
+                df_fma(aqq, q2, q2);
+                df_fma(aqq, q3, q3);
+                df_fma(arq, r.x, q0);
+                df_fma(arq, r.y, q1);
+                df_fma(arq, r.z, q2);
+                df_fma(arq, r.w, q3);
+                df_fma(arp, r.x, c.x);
+                df_fma(arp, r.y, c.y);
+                df_fma(arp, r.z, c.z);
+                df_fma(arp, r.w, c.w);
+            }
+            dots[0] = df_val(apq);
+            dots[1] = df_val(aqq);
+            dots[2] = df_val(arq);
+            dots[3] = df_val(arp);
+        }
+        block_sum<4>(dots, red);
+        const double alpha_d = dots[3] / dots[0];
+        const double rn = rr - 2.0 * alpha_d * dots[2] + alpha_d * alpha_d * dots[1];
+        const float alpha = (float)alpha_d;
+        ++iters;
+        const double rnrm = sqrt(fmax(rn, 0.0));
+        if (!(rn > 0.0) || rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop) {
+            // reliable update in FP64: x += S (e + alpha p), then the true residual
+            for (int k = tid; k < npe; k += nt) {
+                const int off = poff[k];
+                vbox[off] += ((double)ef[off] + (double)alpha * (double)pf[off]) * S_;
+                ef[off] = 0.f;
+            }
+            __syncthreads();
+            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            ++refine;
+            if (rnorm <= stop) break;
+            // r' in the new frame; p' = r' + gamma p with <p', A p> = 0
+            const double sc = 1.0 / rnorm;
+            double a0[2];
+            {
+                DF a = {0.f, 0.f}, b = {0.f, 0.f};
+                for (int k = tid; k < npe; k += nt) {
+                    const int off = poff[k];
+                    const float r = (float)(r64[k] * sc);
+                    rf[off] = r;
+                    df_fma(a, r, r);
+                    df_fma(b, r, qf[off]);
+                }
+                a0[0] = df_val(a);
+                a0[1] = df_val(b);
+            }
+            block_sum<2>(a0, red);
+            const float gamma = (float)(-a0[1] / dots[0]);
+            for (int k = tid; k < npe; k += nt) {
+                const int off = poff[k];
+                pf[off] = rf[off] + gamma * pf[off];
+            }
+            __syncthreads();
+            rr = a0[0];
+            rmax = sqrt(rr);
+            S_ = rnorm;
+            continue;
+        }
+        // ---- pass BC: r -= alpha q, e += alpha p, p = r + beta p ----
+        const float beta = (float)(-(dots[2] - alpha_d * dots[1]) / dots[0]);
+        rr = rn;
+        for (int g = tid; g < ng; g += nt) {
+            const int off = (__ldg(grp + g) >> 4) << 2;
+            const float4 r = ld4(rf + off), q = ld4(qf + off), p_ = ld4(pf + off), e = ld4(ef + off);
+            const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
+            st4(rf + off, r0, r1, r2, r3);
+            st4(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
+            st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
+        }
+        __syncthreads();
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
                                                                  SlotWork W, int inner_shift)
@@ -565,166 +959,29 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *
                 rnorm = sqrt(rr);
             }
         } else {
-            // Mixed: FP32 CG with reliable updates.  The FP32 vectors live in a frame
-            // scaled by S (the true residual norm at the last update), so they stay O(1)
-            // however small the pair density is.  The FP32 correction e accumulates
-            // alpha p; when the recursive residual has dropped by inner_red since the
-            // last update (or reaches the target), x += S e in FP64, the true residual
-            // b - A x is recomputed in FP64 and replaces r, and the search direction is
-            // carried over into the new frame.
-            float *__restrict__ pf = (float *)pbox;
-            float *__restrict__ rf = (float *)rv;
-            float *__restrict__ qf = (float *)qv;
-            float *__restrict__ ef = (float *)ev;
-            const int32_t *__restrict__ poff = S.pe_off;
-            const int npe = S.n_pe;
-            constexpr int U = 4;
-            if (bn > 0.0) {
-                double S_ = bn;
-                double rr;
-                {
-                    double a0[1];
-                    DF a = {0.f, 0.f};
-                    const double sc = 1.0 / S_;
-                    for (int k = tid; k < npe; k += nt) {
-                        const float r = (float)(r64[k] * sc);
-                        rf[k] = r;
-                        ef[k] = 0.f;
-                        pf[poff[k]] = r;
-                        df_fma(a, r, r);
-                    }
-                    a0[0] = df_val(a);
-                    block_sum<1>(a0, red);
-                    rr = a0[0];
-                }
-                double rmax = sqrt(rr);
-                for (;;) {
-                    if (iters >= C.max_iter) {
-                        status = 5;
-                        break;
-                    }
-                    // pass A: q = A p, <p, q>
-                    double pq[1];
-                    {
-                        DF a = {0.f, 0.f};
-                        for (int kb = tid; kb < npe; kb += U * nt) {
-                            int off[U];
-                            float q[U], pc[U];
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int k = kb + u * nt;
-                                off[u] = k < npe ? __ldg(poff + k) : -1;
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                if (off[u] >= 0) {
-                                    pc[u] = pf[off[u]];
-                                    q[u] = -lap_at<float>(pf, off[u], sm.cw32, sm.ds, ndir, fdn, sm.center32);
-                                }
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                if (off[u] >= 0) {
-                                    qf[kb + u * nt] = q[u];
-                                    df_fma(a, pc[u], q[u]);
-                                }
-                            }
-                        }
-                        pq[0] = df_val(a);
-                    }
-                    block_sum<1>(pq, red);
-                    const float alpha = (float)(rr / pq[0]);
-                    // pass B: r -= alpha q, <r, r>
-                    double rn[1];
-                    {
-                        DF a = {0.f, 0.f};
-                        for (int kb = tid; kb < npe; kb += U * nt) {
-                            float rv_[U], qv_[U];
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int k = kb + u * nt;
-                                if (k < npe) {
-                                    rv_[u] = rf[k];
-                                    qv_[u] = qf[k];
-                                }
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int k = kb + u * nt;
-                                if (k < npe) {
-                                    const float r = rv_[u] - alpha * qv_[u];
-                                    rf[k] = r;
-                                    df_fma(a, r, r);
-                                }
-                            }
-                        }
-                        rn[0] = df_val(a);
-                    }
-                    block_sum<1>(rn, red);
-                    ++iters;
-                    const double rnrm = sqrt(rn[0]);
-                    if (rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop || !(rnrm == rnrm)) {
-                        // reliable update in FP64: x += S (e + alpha p)
-                        for (int k = tid; k < npe; k += nt) {
-                            const int off = poff[k];
-                            vbox[off] += ((double)ef[k] + (double)alpha * (double)pf[off]) * S_;
-                            ef[k] = 0.f;
-                        }
-                        __syncthreads();
-                        rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
-                        ++refine;
-                        if (rnorm <= stop) break;
-                        // beta from the replaced residual, direction moved to the new frame
-                        const double Snew = rnorm;
-                        const float bscaled = (float)((rnorm / S_) * (rnorm / S_) / rr * (S_ / Snew));
-                        const double sc = 1.0 / Snew;
-                        double a0[1];
-                        DF a = {0.f, 0.f};
-                        for (int k = tid; k < npe; k += nt) {
-                            const int off = poff[k];
-                            const float r = (float)(r64[k] * sc);
-                            rf[k] = r;
-                            pf[off] = r + bscaled * pf[off];
-                            df_fma(a, r, r);
-                        }
-                        a0[0] = df_val(a);
-                        block_sum<1>(a0, red);
-                        rr = a0[0];
-                        rmax = sqrt(rr);
-                        S_ = Snew;
-                        continue;
-                    }
-                    // pass C: e += alpha p, p = r + beta p
-                    const float beta = (float)(rn[0] / rr);
-                    rr = rn[0];
-                    for (int kb = tid; kb < npe; kb += U * nt) {
-                        int off[U];
-                        float pv_[U], rv_[U], ev_[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const int k = kb + u * nt;
-                            off[u] = k < npe ? __ldg(poff + k) : -1;
-                        }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const int k = kb + u * nt;
-                            if (off[u] >= 0) {
-                                pv_[u] = pf[off[u]];
-                                rv_[u] = rf[k];
-                                ev_[u] = ef[k];
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const int k = kb + u * nt;
-                            if (off[u] >= 0) {
-                                ef[k] = ev_[u] + alpha * pv_[u];
-                                pf[off[u]] = rv_[u] + beta * pv_[u];
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
+            CgMixed cg;
+            cg.S = &S;
+            cg.vbox = vbox;
+            cg.rho = rho;
+            cg.r64 = r64;
+            cg.pf = (float *)pbox;
+            cg.rf = (float *)rv;
+            cg.qf = (float *)qv;
+            cg.ef = (float *)ev;
+            cg.sm = &sm;
+            cg.red = red;
+            cg.ndir = ndir;
+            cg.fdn = fdn;
+            cg.max_iter = C.max_iter;
+            cg.stop = stop;
+            cg.bn = bn;
+            cg.inner_red = inner_red;
+            switch (fdn) {
+            case 1: cg_mixed_v2<1>(cg, iters, refine, status, rnorm); break;
+            case 2: cg_mixed_v2<2>(cg, iters, refine, status, rnorm); break;
+            case 3: cg_mixed_v2<3>(cg, iters, refine, status, rnorm); break;
+            case 4: cg_mixed_v2<4>(cg, iters, refine, status, rnorm); break;
+            default: cg_mixed(cg, iters, refine, status, rnorm); break;
             }
         }
 
@@ -799,6 +1056,15 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *
             const int off = S.pe_off[k];
             vbox[off] = 0.0;
             pbox[off] = (T)0;
+            if (mixed) {
+                // dense FP32 boxes (group path) and compressed vectors (generic path)
+                ((float *)rv)[off] = 0.f;
+                ((float *)qv)[off] = 0.f;
+                ((float *)ev)[off] = 0.f;
+                ((float *)rv)[k] = 0.f;
+                ((float *)qv)[k] = 0.f;
+                ((float *)ev)[k] = 0.f;
+            }
         }
         for (int h = tid; h < S.n_halo; h += nt) vbox[S.halo_off[h]] = 0.0;
         if (tid == 0) {

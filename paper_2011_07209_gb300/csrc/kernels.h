@@ -7,7 +7,10 @@
 namespace exx {
 
 constexpr int kRowThreads = 128;     // pair-list CTA size
-constexpr int kSolveThreads = 1024;  // persistent pair-solver CTA size
+#ifndef EXX_SOLVE_THREADS
+#define EXX_SOLVE_THREADS 1024
+#endif
+constexpr int kSolveThreads = EXX_SOLVE_THREADS;  // persistent pair-solver CTA size
 
 // Per-CTA scratch of the persistent solver: one slot per CTA, all slots equal.
 struct SolveSlots {

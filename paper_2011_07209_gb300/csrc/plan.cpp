@@ -389,9 +389,13 @@ int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L)
         L.c[al] = Hpe[al] + reach[al];
         L.B[al] = 2 * L.c[al] + 1;
     }
+    L.B[2] = (L.B[2] + 3) & ~3;
     L.box = (long long)L.B[0] * L.B[1] * L.B[2];
     if (L.box > (1LL << 30)) return EXX_ERR_ARG;
-    for (int d = 0; d < st.ndir; ++d) L.dstride[d] = (st.dir[d][0] * L.B[1] + st.dir[d][1]) * L.B[2] + st.dir[d][2];
+    for (int d = 0; d < st.ndir; ++d) {
+        L.dstride[d] = (st.dir[d][0] * L.B[1] + st.dir[d][1]) * L.B[2] + st.dir[d][2];
+        L.rstride[d] = (st.dir[d][0] * L.B[1] + st.dir[d][1]) * L.B[2];
+    }
     L.gstride[0] = L.B[1] * L.B[2];
     L.gstride[1] = L.B[2];
     L.gstride[2] = 1;
@@ -440,6 +444,21 @@ int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L)
             if (pass == 0) L.halo_off.push_back(box_off(m));
         }
     L.n_halo = (int)L.halo_off.size();
+    // aligned 4-point groups: PE rows are runs of equal (m0, m1) in the lexicographic list
+    for (int q = 0; q < o.n_pe;) {
+        int e = q;
+        while (e < o.n_pe && o.m[3 * e] == o.m[3 * q] && o.m[3 * e + 1] == o.m[3 * q + 1]) ++e;
+        const int lo = o.m[3 * q + 2] + L.c[2], hi = o.m[3 * (e - 1) + 2] + L.c[2];   // box columns
+        const long long row = ((long long)(o.m[3 * q] + L.c[0]) * L.B[1] + (o.m[3 * q + 1] + L.c[1])) * L.B[2];
+        for (int g = lo & ~3; g <= hi; g += 4) {
+            int mask = 0;
+            for (int i = 0; i < 4; ++i)
+                if (g + i >= lo && g + i <= hi) mask |= 1 << i;
+            const long long off = row + g;
+            L.groups.push_back((int32_t)(((off >> 2) << 4) | mask));
+        }
+        q = e;
+    }
     return EXX_OK;
 }
 

@@ -54,6 +54,9 @@ int make_offsets(const Metric &mt, double r_pe, double r_me, OffsetSet &o);
 //   box: PE bounding box plus the stencil reach on every side; element of
 //   offset m sits at ((m0 + c0) B1 + (m1 + c1)) B2 + (m2 + c2).
 //   shell points are reordered: halo (reached by a stencil from PE) first.
+//   B2 is padded to a multiple of 4 so that rows start on 16-byte boundaries;
+//   groups are the 4-aligned runs of 4 box elements along the last axis that
+//   hold at least one PE point, packed as (offset / 4) << 4 | PE mask.
 struct SetLayout {
     int n_pe = 0, n_shell = 0, n_halo = 0;
     int B[3] = {}, c[3] = {};
@@ -62,6 +65,8 @@ struct SetLayout {
     int gstride[3] = {};
     std::vector<int32_t> pe_m, pe_off;     // packed offsets and box offsets of PE points
     std::vector<int32_t> sh_m, halo_off;   // packed offsets of shell points; box offsets of halo points
+    std::vector<int32_t> groups;           // aligned 4-point groups covering PE
+    int rstride[6] = {};                   // box stride of a direction without its last-axis part
 };
 int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
 
