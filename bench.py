@@ -126,7 +126,7 @@ def kernel_sha():
 
 
 def algorithmic_bytes(n_pairs, total_iter, total_refine, n_pe, n_me, s):
-    """Bytes the pair solver must move per launch ("Algorithmic bytes"):
+    """Bytes the pair solver must move per launch:
     CG: 7 N_PE s per iteration (x, r, p read + written, p read by the stencil);
     refinement: 3 N_PE 8 per FP64 residual (v, rho read, r written);
     per pair: gather 2 N_ME 8, D read-modify-write 2 N_ME 16, rho 8 N_PE."""

@@ -20,9 +20,8 @@
  *   - E_xx, D_xx and sigma_xx / Pi_xx                          (Eqs. exxGen_mlwf, Dxx,
  *                                                                sxx_working, pixx_working)
  *
- * Every floating-point value is double precision.  Readings of points the
- * paper leaves open are listed in the design doc of the repository and repeated
- * at the code that implements them.
+ * Every floating-point value is double precision.  Where the paper leaves a
+ * point open, the reading taken is stated at the code that implements it.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared -o liboracle.so exx_oracle.c -lm
  */

@@ -310,6 +310,15 @@ __device__ __forceinline__ void df_fma(DF &acc, float a, float b)
     acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, pe));
 }
 __device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
+// TwoSum of a float into the double-float accumulator.
+__device__ __forceinline__ void df_add(DF &acc, float x)
+{
+    const float s = __fadd_rn(acc.hi, x);
+    const float bb = __fadd_rn(s, -acc.hi);
+    const float err = __fadd_rn(__fadd_rn(acc.hi, -__fadd_rn(s, -bb)), __fadd_rn(x, -bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, err);
+}
 
 // ---------------------------------------------------------------------------
 // Orbital access.
@@ -700,22 +709,12 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
                 const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
                 st4(qf + off, q0, q1, q2, q3);
                 const float4 r = ld4(rf + off);
-                df_fma(apq, c.x, q0);
-                df_fma(apq, c.y, q1);
-                df_fma(apq, c.z, q2);
-                df_fma(apq, c.w, q3);
-                df_fma(aqq, q0, q0);
-                df_fma(aqq, q1, q1);
-                df_fma(aqq, q2, q2);
-                df_fma(aqq, q3, q3);
-                df_fma(arq, r.x, q0);
-                df_fma(arq, r.y, q1);
-                df_fma(arq, r.z, q2);
-                df_fma(arq, r.w, q3);
-                df_fma(arp, r.x, c.x);
-                df_fma(arp, r.y, c.y);
-                df_fma(arp, r.z, c.z);
-                df_fma(arp, r.w, c.w);
+                // the four products of a group are summed in FP32, the group sums
+                // in double-float
+                df_add(apq, c.x * q0 + c.y * q1 + c.z * q2 + c.w * q3);
+                df_add(aqq, q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+                df_add(arq, r.x * q0 + r.y * q1 + r.z * q2 + r.w * q3);
+                df_add(arp, r.x * c.x + r.y * c.y + r.z * c.z + r.w * c.w);
             }
             dots[0] = df_val(apq);
             dots[1] = df_val(aqq);
@@ -782,7 +781,7 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
 }
 
 template <class T>
-__global__ void __launch_bounds__(kSolveThreads, 1) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
                                                                  SlotWork W, int inner_shift)
 {
     __shared__ SmemCell sm;

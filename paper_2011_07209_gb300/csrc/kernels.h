@@ -10,7 +10,11 @@ constexpr int kRowThreads = 128;     // pair-list CTA size
 #ifndef EXX_SOLVE_THREADS
 #define EXX_SOLVE_THREADS 1024
 #endif
-constexpr int kSolveThreads = EXX_SOLVE_THREADS;  // persistent pair-solver CTA size
+#ifndef EXX_SOLVE_MIN_BLOCKS
+#define EXX_SOLVE_MIN_BLOCKS 1
+#endif
+constexpr int kSolveThreads = EXX_SOLVE_THREADS;       // persistent pair-solver CTA size
+constexpr int kSolveMinBlocks = EXX_SOLVE_MIN_BLOCKS;  // resident CTAs per SM it is compiled for
 
 // Per-CTA scratch of the persistent solver: one slot per CTA, all slots equal.
 struct SolveSlots {
