@@ -186,6 +186,27 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
  * EXX_ERR_CAPACITY if it exceeds cap. */
 int exx_get_pair_list(exx_plan *plan, int cap, int *n, int *rows);
 
+/* The unique pair list of one cell (the same rows, bit for bit, as
+ * exx_get_pair_list after a solve) for callers that cannot allocate device
+ * memory when they need it -- for instance code that runs while a CUDA graph
+ * is captured under a fixed memory budget, or inside an engine whose device
+ * memory is handed out once by its own pool.  The paper has no counterpart:
+ * this is a deployment convenience.
+ *   cell:     host struct; centres: device [n_orb][3]; r_pair: cutoff (bohr)
+ *   rows:     device [cap][8] output rows (i, j, k0, k1, k2, g0, g1, g2);
+ *             rows past cap are not written
+ *   n_pairs:  device int, receives the total number of pairs (may exceed cap)
+ * The call allocates nothing: its scratch (row counts and offsets) is a
+ * static device array sized for n_orb <= 16384 (128 KB), held by every GPU
+ * that loads the library until the process exits; larger n_orb returns
+ * EXX_ERR_CAPACITY.  The first call on a device resolves that array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Every call shares the array, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race.  The work is enqueued
+ * on `stream` and the call returns without waiting for it. */
+int exx_pair_list_noalloc(const exx_cell *cell, const double *centres, int n_orb, double r_pair, int cap,
+                          int *rows, int *n_pairs, void *stream);
+
 /* Index half-widths of a D box that holds every contribution of the pairs of
  * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);

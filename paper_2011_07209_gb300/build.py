@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libexx.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels.cu", "api.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
 CPP_SOURCES = ["plan.cpp"]
 
 

@@ -25,7 +25,8 @@ _lock = threading.Lock()
 
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
-           "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version")
+           "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version",
+           "exx_pair_list_noalloc")
 
 
 class Cell(C.Structure):
@@ -103,6 +104,8 @@ def lib(build_if_missing: bool = False):
             L.exx_get_pair_list.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.exx_dbox_halfwidth.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(C.c_int)]
             L.exx_ctx_set_timing.argtypes = [C.c_void_p, C.c_int]
+            L.exx_pair_list_noalloc.argtypes = [C.POINTER(Cell), C.c_void_p, C.c_int, C.c_double, C.c_int,
+                                                C.c_void_p, C.c_void_p, C.c_void_p]
             L.exx_ctx_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
             _lib = L
     return _lib
@@ -297,3 +300,12 @@ def result_dict(r: Result) -> dict:
             "stress": np.array(list(r.stress)).reshape(3, 3), "n_pairs": r.n_pairs, "n_aux": r.n_aux,
             "n_stcl": r.n_stcl, "max_cg_iter": r.max_cg_iter, "total_cg_iter": r.total_cg_iter,
             "max_refine": r.max_refine, "failed_pair": r.failed_pair, "total_refine": r.total_refine}
+
+
+def pair_list_noalloc(lattice, n, centres, n_orb, r_pair, rows, n_pairs, stream=None) -> int:
+    """exx_pair_list_noalloc: centres, rows ([cap][8] int32) and n_pairs (int32) are
+    device buffers (torch tensors); returns the status code."""
+    cap = int(rows.shape[0]) if rows is not None else 0
+    s = C.c_void_p(stream) if isinstance(stream, int) else stream
+    return lib().exx_pair_list_noalloc(C.byref(make_cell(lattice, n)), _ptr(centres), int(n_orb), float(r_pair), cap,
+                                       _ptr(rows), _ptr(n_pairs), s)
