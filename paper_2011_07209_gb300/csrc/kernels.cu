@@ -660,12 +660,17 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
         rr = a0[0];
     }
     double rmax = sqrt(rr);
+    // <r,r> of the FP32 residual is summed afresh in pass BC (per-warp partials,
+    // double-buffered by iteration parity) and read after the next pass A, so the
+    // stopping test never rests on a long recurrence
+    __shared__ double s_rrw[2][32];
+    bool rr_pending = false;
     for (;;) {
         if (iters >= cg.max_iter) {
             status = 5;
             break;
         }
-        // ---- pass A: q = A p on every group, <p,q>, <q,q>, <r,q> ----
+        // ---- pass A: q = A p on every group, <p,q>, <q,q>, <r,q>, <r,p> ----
         double dots[4];
         {
             DF apq = {0.f, 0.f}, aqq = {0.f, 0.f}, arq = {0.f, 0.f}, arp = {0.f, 0.f};
@@ -722,16 +727,24 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
             dots[3] = df_val(arp);
         }
         block_sum<4>(dots, red);
+        if (rr_pending) {
+            const int lane = tid & 31;
+            rr = warp_sum(lane < (nt >> 5) ? s_rrw[(iters - 1) & 1][lane] : 0.0);
+        }
         const double alpha_d = dots[3] / dots[0];
         const double rn = rr - 2.0 * alpha_d * dots[2] + alpha_d * alpha_d * dots[1];
         const float alpha = (float)alpha_d;
         ++iters;
         const double rnrm = sqrt(fmax(rn, 0.0));
-        if (!(rn > 0.0) || rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop) {
+        // a breakdown (p A p or r p not positive, or not finite) also takes the
+        // FP64 path, which restarts from the true residual
+        const bool breakdown = !(dots[0] > 0.0) || !(dots[3] > 0.0) || !(alpha_d < 1e300);
+        if (breakdown || !(rn > 0.0) || rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop) {
+            const float alpha_u = breakdown ? 0.f : alpha;
             // reliable update in FP64: x += S (e + alpha p), then the true residual
             for (int k = tid; k < npe; k += nt) {
                 const int off = poff[k];
-                vbox[off] += ((double)ef[off] + (double)alpha * (double)pf[off]) * S_;
+                vbox[off] += ((double)ef[off] + (double)alpha_u * (double)pf[off]) * S_;
                 ef[off] = 0.f;
             }
             __syncthreads();
@@ -754,13 +767,14 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
                 a0[1] = df_val(b);
             }
             block_sum<2>(a0, red);
-            const float gamma = (float)(-a0[1] / dots[0]);
+            const float gamma = breakdown ? 0.f : (float)(-a0[1] / dots[0]);
             for (int k = tid; k < npe; k += nt) {
                 const int off = poff[k];
                 pf[off] = rf[off] + gamma * pf[off];
             }
             __syncthreads();
             rr = a0[0];
+            rr_pending = false;
             rmax = sqrt(rr);
             S_ = rnorm;
             continue;
@@ -768,13 +782,20 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
         // ---- pass BC: r -= alpha q, e += alpha p, p = r + beta p ----
         const float beta = (float)(-(dots[2] - alpha_d * dots[1]) / dots[0]);
         rr = rn;
+        rr_pending = true;
+        DF arr = {0.f, 0.f};
         for (int g = tid; g < ng; g += nt) {
             const int off = (__ldg(grp + g) >> 4) << 2;
             const float4 r = ld4(rf + off), q = ld4(qf + off), p_ = ld4(pf + off), e = ld4(ef + off);
             const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
+            df_add(arr, r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
             st4(rf + off, r0, r1, r2, r3);
             st4(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
             st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
+        }
+        {
+            const double w = warp_sum(df_val(arr));
+            if ((tid & 31) == 0) s_rrw[(iters - 1) & 1][tid >> 5] = w;
         }
         __syncthreads();
     }
