@@ -320,6 +320,48 @@ __device__ __forceinline__ void df_add(DF &acc, float x)
     acc.lo = __fadd_rn(acc.lo, err);
 }
 
+// Sum of two double-float values (TwoSum on the high parts).
+__device__ __forceinline__ DF df_sum(DF a, DF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fadd_rn(s, -a.hi);
+    const float err = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -bb)), __fadd_rn(b.hi, -bb));
+    return {s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+
+// Sum K double-float values over the CTA in FP32 arithmetic; the totals end up
+// in every lane of warp 0 (the scalar work that follows runs there, so the
+// SM's FP64 pipe is not loaded by a thousand redundant copies of it).
+template <int K>
+__device__ __forceinline__ void block_sum_df(DF (&v)[K], float2 *red2)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF t = {__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+            v[k] = df_sum(v[k], t);
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red2[w * K + k] = make_float2(v[k].hi, v[k].lo);
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 t = lane < nw ? red2[lane * K + k] : make_float2(0.f, 0.f);
+            v[k] = {t.x, t.y};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const DF u = {__shfl_xor_sync(0xffffffffu, v[k].hi, o), __shfl_xor_sync(0xffffffffu, v[k].lo, o)};
+                v[k] = df_sum(v[k], u);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Orbital access.
 // ---------------------------------------------------------------------------
@@ -597,25 +639,99 @@ __device__ __forceinline__ void st4(float *p, float a, float b, float c, float d
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
 
-// Mixed-precision Poisson solve of one pair on aligned 4-point groups.
-//
-// Same algorithm as cg_mixed (FP32 CG in a frame scaled by the last true
-// residual norm, FP64 reliable updates), restructured for bandwidth:
-//   * every FP32 vector (p, r, q, e) is a dense box, zero outside PE, and the
-//     passes walk the list of aligned 4-point groups with 16-byte accesses;
-//   * the stencil reads p with aligned float4 loads for the directions that do
-//     not step along the last axis, a 12-wide register window for the last
-//     axis, and scalar loads for auxiliary directions with a last-axis step;
-//   * one reduction per iteration: pass A forms q = A p together with <p,q>,
-//     <q,q>, <r,q> and <r,p>; then alpha = <r,p>/<p,q> (exact line search),
-//     <r',r'> = <r,r> - 2 alpha <r,q> + alpha^2 <q,q>, and the Hestenes-Stiefel
-//     beta = -(<r,q> - alpha <q,q>) / <p,q> keeps p' A-conjugate to p, so r, e
-//     and p are updated in one fused pass.  These forms stay exact when an FP64
-//     residual replacement has perturbed the Krylov relations; after a
-//     replacement the new direction is r' + gamma p with gamma chosen to keep
-//     it A-conjugate to the last direction.
+// q = -(L p) on the PE lanes of one aligned group (zero on the others), stored,
+// with the four products <p,q>, <q,q>, <r,q>, <r,p> of the group added to the
+// double-float dot accumulators.
 template <int FDN>
-__device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
+__device__ __forceinline__ void stencil_group(const float *__restrict__ pf, const float *__restrict__ rf,
+                                              float *__restrict__ qf, int32_t gw, const float (*cw)[8], float center,
+                                              const int *rs, const int *dsf, const int *d2, int ndir, DF &apq, DF &aqq,
+                                              DF &arq, DF &arp)
+{
+    const int off = (gw >> 4) << 2;
+    const int mask = gw & 15;
+    const float4 c = ld4(pf + off);
+    const float4 cm = ld4(pf + off - 4);
+    const float4 cp = ld4(pf + off + 4);
+    const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
+    float acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
+#pragma unroll
+    for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (d == 2 || d >= ndir) continue;
+        if (d2[d] == 0) {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_) {
+                const float4 a = ld4(pf + off + s_ * rs[d]);
+                const float4 b = ld4(pf + off - s_ * rs[d]);
+                acc[0] += cw[d][s_] * (a.x + b.x);
+                acc[1] += cw[d][s_] * (a.y + b.y);
+                acc[2] += cw[d][s_] * (a.z + b.z);
+                acc[3] += cw[d][s_] * (a.w + b.w);
+            }
+        } else {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (pf[off + i + s_ * dsf[d]] + pf[off + i - s_ * dsf[d]]);
+        }
+    }
+    const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
+    const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
+    st4(qf + off, q0, q1, q2, q3);
+    const float4 r = ld4(rf + off);
+    df_add(apq, c.x * q0 + c.y * q1 + c.z * q2 + c.w * q3);
+    df_add(aqq, q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    df_add(arq, r.x * q0 + r.y * q1 + r.z * q2 + r.w * q3);
+    df_add(arp, r.x * c.x + r.y * c.y + r.z * c.z + r.w * c.w);
+}
+
+// r -= alpha q, e += alpha p, p = r + beta p on one aligned group, with <r,r>
+// of the updated residual added to a double-float accumulator.
+__device__ __forceinline__ void update_group(float *__restrict__ rf, float *__restrict__ ef, float *__restrict__ pf,
+                                             const float *__restrict__ qf, int off, float alpha, float beta, DF &arr)
+{
+    const float4 r = ld4(rf + off), q = ld4(qf + off), p_ = ld4(pf + off), e = ld4(ef + off);
+    const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
+    df_add(arr, r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    st4(rf + off, r0, r1, r2, r3);
+    st4(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
+    st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
+}
+
+constexpr int kSweepChunkGroups = 8;   // groups per thread between two CTA barriers of the sweep
+constexpr int kMaxSweepChunks = 512;   // chunks the one-sweep path can order
+
+// Mixed-precision Poisson solve of one pair in ONE sweep over the vectors per
+// iteration: FP32 CG in a frame scaled by the last true residual norm, with
+// FP64 reliable updates, on the dense box of aligned 4-point groups.
+//   * every FP32 vector (p, r, q, e) is a dense box, zero outside PE; the stencil
+//     reads p with aligned float4 loads for the directions that do not step
+//     along the last axis, a 12-wide register window for the last axis, and
+//     scalar loads for auxiliary directions with a last-axis step;
+//   * one reduction per iteration: the stencil sweep forms q = A p with <p,q>,
+//     <q,q>, <r,q>, <r,p> (and <r,r> of the residual it has just updated); then
+//     alpha = <r,p>/<p,q> (exact line search), the predicted
+//     <r',r'> = <r,r> - 2 alpha <r,q> + alpha^2 <q,q> decides the FP64
+//     replacement, and the Hestenes-Stiefel beta = -(<r,q> - alpha <q,q>)/<p,q>
+//     keeps p' A-conjugate to p.  These forms stay exact when a replacement has
+//     perturbed the Krylov relations; after one the new direction is
+//     r' + gamma p with gamma chosen to keep it A-conjugate to the last one.
+// The update r -= alpha q, e += alpha p, p = r + beta p of iteration k is not a pass of its
+// own: it runs inside the stencil sweep of iteration k+1, ahead of it.  The
+// groups are sorted by box offset, so the stencil of a chunk of groups reads p
+// only up to a known group index (the chunk's last offset plus the stencil
+// reach); the update front is kept past that index before the chunk's stencil
+// runs, with one CTA barrier per chunk.  The stencil then reads p and r just
+// written by the update (cache-resident), and every vector crosses HBM once
+// per iteration: r, e, p, q read, r, e, p, q written.
+template <int FDN>
+__device__ __noinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
 {
     const SetDev &S = *cg.S;
     const SmemCell &sm = *cg.sm;
@@ -630,16 +746,35 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
     const int32_t *__restrict__ grp = S.groups;
     double *red = cg.red;
     const int npe = S.n_pe, ng = S.n_groups;
-    const int ndir = cg.ndir, fdn = cg.fdn;
+    const int ndir = cg.ndir;
     const double stop = cg.stop, inner_red = cg.inner_red;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (!(cg.bn > 0.0)) return;
-
-    // coefficients and strides are read from shared memory (broadcast) to keep
-    // the register budget of 1024-thread CTAs
     const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
     const float(*cw)[8] = sm.cw32;
     const float center = sm.center32;
+
+    // update front needed by each chunk: the number of groups whose offset is at
+    // most the chunk's last offset plus the stencil reach
+    __shared__ int s_need[kMaxSweepChunks];
+    const int W = kSweepChunkGroups * nt;   // groups per chunk
+    const int nchunk = (ng + W - 1) / W;
+    {
+        int reach = 7;
+        for (int d = 0; d < ndir; ++d)
+            reach = max(reach, 3 + FDN * max(abs(dsf[d]), abs(rs[d])));
+        for (int c = tid; c < nchunk; c += nt) {
+            const int last = min(ng, (c + 1) * W) - 1;
+            const long long lim = (long long)((grp[last] >> 4) << 2) + reach;
+            int lo = last + 1, hi = ng;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)((grp[mid] >> 4) << 2) <= lim) lo = mid + 1;
+                else hi = mid;
+            }
+            s_need[c] = lo;
+        }
+    }
 
     double S_ = cg.bn;
     double rr;
@@ -659,145 +794,111 @@ __device__ __noinline__ void cg_mixed_v2(const CgMixed &cg, int &iters, int &ref
         block_sum<1>(a0, red);
         rr = a0[0];
     }
-    double rmax = sqrt(rr);
-    // <r,r> of the FP32 residual is summed afresh in pass BC (per-warp partials,
-    // double-buffered by iteration parity) and read after the next pass A, so the
-    // stopping test never rests on a long recurrence
-    __shared__ double s_rrw[2][32];
-    bool rr_pending = false;
+    // scalars of the iteration, kept by thread 0 and broadcast through shared memory
+    __shared__ struct {
+        double rr, rmax, S, pq;
+        float alpha, beta;
+        int act;   // 0 continue, 1 FP64 replacement, 2 replacement after a breakdown
+    } cs;
+    if (tid == 0) {
+        cs.rr = rr;
+        cs.rmax = sqrt(rr);
+        cs.S = cg.bn;
+    }
+    __syncthreads();
+    float2 *red2 = reinterpret_cast<float2 *>(red);
+    bool pending = false;          // an update (alpha_p, beta_p) waits for the next sweep
+    float alpha_p = 0.f, beta_p = 0.f;
     for (;;) {
         if (iters >= cg.max_iter) {
             status = 5;
             break;
         }
-        // ---- pass A: q = A p on every group, <p,q>, <q,q>, <r,q>, <r,p> ----
-        double dots[4];
-        {
-            DF apq = {0.f, 0.f}, aqq = {0.f, 0.f}, arq = {0.f, 0.f}, arp = {0.f, 0.f};
-            for (int g = tid; g < ng; g += nt) {
-                const int32_t gw = __ldg(grp + g);
-                const int off = (gw >> 4) << 2;
-                const int mask = gw & 15;
-                const float4 c = ld4(pf + off);
-                const float4 cm = ld4(pf + off - 4);
-                const float4 cp = ld4(pf + off + 4);
-                const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
-                float acc[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
-#pragma unroll
-                for (int s_ = 1; s_ <= FDN; ++s_)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
-#pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    if (d == 2 || d >= ndir) continue;
-                    if (d2[d] == 0) {
-#pragma unroll
-                        for (int s_ = 1; s_ <= FDN; ++s_) {
-                            const float4 a = ld4(pf + off + s_ * rs[d]);
-                            const float4 b = ld4(pf + off - s_ * rs[d]);
-                            acc[0] += cw[d][s_] * (a.x + b.x);
-                            acc[1] += cw[d][s_] * (a.y + b.y);
-                            acc[2] += cw[d][s_] * (a.z + b.z);
-                            acc[3] += cw[d][s_] * (a.w + b.w);
-                        }
-                    } else {
-#pragma unroll
-                        for (int s_ = 1; s_ <= FDN; ++s_)
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                acc[i] += cw[d][s_] * (pf[off + i + s_ * dsf[d]] + pf[off + i - s_ * dsf[d]]);
-                    }
+        DF dv[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // <p,q> <q,q> <r,q> <r,p> <r,r>
+        if (!pending) {
+            for (int g = tid; g < ng; g += nt)
+                stencil_group<FDN>(pf, rf, qf, __ldg(grp + g), cw, center, rs, dsf, d2, ndir, dv[0], dv[1], dv[2],
+                                   dv[3]);
+        } else {
+            int front = 0;
+            for (int c = 0; c < nchunk; ++c) {
+                const int need = s_need[c];
+                for (; front < need; front += nt) {
+                    const int g = front + tid;
+                    if (g < ng) update_group(rf, ef, pf, qf, (__ldg(grp + g) >> 4) << 2, alpha_p, beta_p, dv[4]);
                 }
-                const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
-                const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
-                st4(qf + off, q0, q1, q2, q3);
-                const float4 r = ld4(rf + off);
-                // the four products of a group are summed in FP32, the group sums
-                // in double-float
-                df_add(apq, c.x * q0 + c.y * q1 + c.z * q2 + c.w * q3);
-                df_add(aqq, q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-                df_add(arq, r.x * q0 + r.y * q1 + r.z * q2 + r.w * q3);
-                df_add(arp, r.x * c.x + r.y * c.y + r.z * c.z + r.w * c.w);
+                __syncthreads();
+                const int gend = min(ng, (c + 1) * W);
+                for (int g = c * W + tid; g < gend; g += nt)
+                    stencil_group<FDN>(pf, rf, qf, __ldg(grp + g), cw, center, rs, dsf, d2, ndir, dv[0], dv[1], dv[2],
+                                       dv[3]);
             }
-            dots[0] = df_val(apq);
-            dots[1] = df_val(aqq);
-            dots[2] = df_val(arq);
-            dots[3] = df_val(arp);
         }
-        block_sum<4>(dots, red);
-        if (rr_pending) {
-            const int lane = tid & 31;
-            rr = warp_sum(lane < (nt >> 5) ? s_rrw[(iters - 1) & 1][lane] : 0.0);
+        block_sum_df<5>(dv, red2);
+        if (tid == 0) {
+            double d[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) d[k] = (double)dv[k].hi + (double)dv[k].lo;
+            const double rr_ = pending ? d[4] : cs.rr;
+            const double alpha_d = d[3] / d[0];
+            const double rn = rr_ - 2.0 * alpha_d * d[2] + alpha_d * alpha_d * d[1];
+            const double rnrm = sqrt(fmax(rn, 0.0));
+            const bool breakdown = !(d[0] > 0.0) || !(d[3] > 0.0) || !(alpha_d < 1e300);
+            int act = 0;
+            if (breakdown) act = 2;
+            else if (!(rn > 0.0) || rnrm <= inner_red * cs.rmax || rnrm * cs.S <= 0.5 * stop) act = 1;
+            cs.alpha = breakdown ? 0.f : (float)alpha_d;
+            cs.beta = breakdown ? 0.f : (float)(-(d[2] - alpha_d * d[1]) / d[0]);
+            cs.pq = d[0];
+            cs.rr = rn;
+            cs.act = act;
         }
-        const double alpha_d = dots[3] / dots[0];
-        const double rn = rr - 2.0 * alpha_d * dots[2] + alpha_d * alpha_d * dots[1];
-        const float alpha = (float)alpha_d;
+        __syncthreads();
+        const int act = cs.act;
+        const float alpha = cs.alpha;
+        pending = false;
         ++iters;
-        const double rnrm = sqrt(fmax(rn, 0.0));
-        // a breakdown (p A p or r p not positive, or not finite) also takes the
-        // FP64 path, which restarts from the true residual
-        const bool breakdown = !(dots[0] > 0.0) || !(dots[3] > 0.0) || !(alpha_d < 1e300);
-        if (breakdown || !(rn > 0.0) || rnrm <= inner_red * rmax || rnrm * S_ <= 0.5 * stop) {
-            const float alpha_u = breakdown ? 0.f : alpha;
-            // reliable update in FP64: x += S (e + alpha p), then the true residual
+        if (act) {
+            const double S_ = cs.S;
             for (int k = tid; k < npe; k += nt) {
                 const int off = poff[k];
-                vbox[off] += ((double)ef[off] + (double)alpha_u * (double)pf[off]) * S_;
+                vbox[off] += ((double)ef[off] + (double)alpha * (double)pf[off]) * S_;
                 ef[off] = 0.f;
             }
             __syncthreads();
-            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, cg.fdn, sm.center64, red));
             ++refine;
             if (rnorm <= stop) break;
-            // r' in the new frame; p' = r' + gamma p with <p', A p> = 0
             const double sc = 1.0 / rnorm;
-            double a0[2];
-            {
-                DF a = {0.f, 0.f}, b = {0.f, 0.f};
-                for (int k = tid; k < npe; k += nt) {
-                    const int off = poff[k];
-                    const float r = (float)(r64[k] * sc);
-                    rf[off] = r;
-                    df_fma(a, r, r);
-                    df_fma(b, r, qf[off]);
-                }
-                a0[0] = df_val(a);
-                a0[1] = df_val(b);
+            DF ab[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            for (int k = tid; k < npe; k += nt) {
+                const int off = poff[k];
+                const float r = (float)(r64[k] * sc);
+                rf[off] = r;
+                df_fma(ab[0], r, r);
+                df_fma(ab[1], r, qf[off]);
             }
-            block_sum<2>(a0, red);
-            const float gamma = breakdown ? 0.f : (float)(-a0[1] / dots[0]);
+            block_sum_df<2>(ab, red2);
+            if (tid == 0) {
+                const double rr_ = (double)ab[0].hi + (double)ab[0].lo;
+                const double rq_ = (double)ab[1].hi + (double)ab[1].lo;
+                cs.beta = act == 2 ? 0.f : (float)(-rq_ / cs.pq);   // gamma of the carried direction
+                cs.rr = rr_;
+                cs.rmax = sqrt(rr_);
+                cs.S = rnorm;
+            }
+            __syncthreads();
+            const float gamma = cs.beta;
             for (int k = tid; k < npe; k += nt) {
                 const int off = poff[k];
                 pf[off] = rf[off] + gamma * pf[off];
             }
             __syncthreads();
-            rr = a0[0];
-            rr_pending = false;
-            rmax = sqrt(rr);
-            S_ = rnorm;
             continue;
         }
-        // ---- pass BC: r -= alpha q, e += alpha p, p = r + beta p ----
-        const float beta = (float)(-(dots[2] - alpha_d * dots[1]) / dots[0]);
-        rr = rn;
-        rr_pending = true;
-        DF arr = {0.f, 0.f};
-        for (int g = tid; g < ng; g += nt) {
-            const int off = (__ldg(grp + g) >> 4) << 2;
-            const float4 r = ld4(rf + off), q = ld4(qf + off), p_ = ld4(pf + off), e = ld4(ef + off);
-            const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
-            df_add(arr, r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-            st4(rf + off, r0, r1, r2, r3);
-            st4(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
-            st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
-        }
-        {
-            const double w = warp_sum(df_val(arr));
-            if ((tid & 31) == 0) s_rrw[(iters - 1) & 1][tid >> 5] = w;
-        }
-        __syncthreads();
+        alpha_p = alpha;
+        beta_p = cs.beta;
+        pending = true;
     }
 }
 
@@ -996,12 +1097,16 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             cg.stop = stop;
             cg.bn = bn;
             cg.inner_red = inner_red;
-            switch (fdn) {
-            case 1: cg_mixed_v2<1>(cg, iters, refine, status, rnorm); break;
-            case 2: cg_mixed_v2<2>(cg, iters, refine, status, rnorm); break;
-            case 3: cg_mixed_v2<3>(cg, iters, refine, status, rnorm); break;
-            case 4: cg_mixed_v2<4>(cg, iters, refine, status, rnorm); break;
-            default: cg_mixed(cg, iters, refine, status, rnorm); break;
+            if ((S.n_groups + kSweepChunkGroups * nt - 1) / (kSweepChunkGroups * nt) <= kMaxSweepChunks) {
+                switch (fdn) {
+                case 1: cg_mixed_sweep<1>(cg, iters, refine, status, rnorm); break;
+                case 2: cg_mixed_sweep<2>(cg, iters, refine, status, rnorm); break;
+                case 3: cg_mixed_sweep<3>(cg, iters, refine, status, rnorm); break;
+                case 4: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
+                default: cg_mixed(cg, iters, refine, status, rnorm); break;
+                }
+            } else {
+                cg_mixed(cg, iters, refine, status, rnorm);
             }
         }
 
