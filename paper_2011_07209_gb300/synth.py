@@ -54,6 +54,11 @@ class MLWFSet:
     def n_orb(self) -> int:
         return int(self.centres.shape[0])
 
+    def subset(self, k: int) -> "MLWFSet":
+        """The first k orbitals of the cell (same grid and boxes)."""
+        return MLWFSet(lattice=self.lattice, n=self.n, centres=self.centres[:k].copy(), a=self.a[:k].copy(),
+                       box=self.box, box_lo=self.box_lo[:k].copy(), phi=self.phi[:k].copy(), s=self.s)
+
     @property
     def volume(self) -> float:
         return float(abs(np.linalg.det(self.lattice)))
