@@ -73,6 +73,16 @@ typedef enum {
 
 enum { EXX_FP64 = 0, EXX_MIXED = 1 };          /* exx_params.precision */
 enum { EXX_MEM_DEVICE = 0, EXX_MEM_HOST = 1 };  /* memory kind of caller buffers */
+/* exx_params.stress_mode (Sec. II C, "Isotropic Constraints"):
+ *   EXX_STRESS_FULL       sigma and the full Pi_xx^pot (Eqs. sxx_working, pixx_working);
+ *   EXX_STRESS_ISOTROPIC  sigma as above, Pi_xx^pot replaced by p_int delta_ab with
+ *                         p_int = Tr Pi / 3 (Eq. pxx_working);
+ *   EXX_STRESS_CUBIC      simple cubic cells only (lattice = L I): the sigma integrals
+ *                         are skipped and p_int = E_xx / (3V) (Eq. liq_press), Pi =
+ *                         p_int delta_ab, sigma^{a alpha} = -E_xx / (3L) delta_{a alpha}
+ *                         (so that Tr sigma = dE_xx/dL = -E_xx/L, Eq. dexxdL).  Any
+ *                         other cell returns EXX_ERR_ARG. */
+enum { EXX_STRESS_FULL = 0, EXX_STRESS_ISOTROPIC = 1, EXX_STRESS_CUBIC = 2 };
 
 typedef struct exx_ctx exx_ctx;
 typedef struct exx_plan exx_plan;
@@ -99,6 +109,15 @@ typedef struct {
     int frozen;             /* 1: subdomain offsets and NK aux directions stay those of the */
                             /* plan's cell while h changes (fixed number of points,         */
                             /* Sec. III B 2); 0: rebuilt whenever the cell changes          */
+    int stress_mode;        /* EXX_STRESS_FULL (0), EXX_STRESS_ISOTROPIC or EXX_STRESS_CUBIC */
+    int warm_start;         /* 1: each pair's CG starts from that pair's solution of the     */
+                            /* previous solve with this plan (same i, j and lattice image;   */
+                            /* shifted by the change of the grid-resolved pair centre; zero  */
+                            /* where the shifted point leaves PE) -- the guess from the      */
+                            /* previous MD step of Sec. III B 2.  The plan keeps one FP32    */
+                            /* solution per pair (2 x n_pairs x N_PE x 4 bytes of device     */
+                            /* memory).  The stopping rule is unchanged (|b - A v| <= tol |b|). */
+                            /* 0: every CG starts from v = 0.                                 */
 } exx_params;
 
 typedef struct {
@@ -132,6 +151,9 @@ typedef struct {
     int max_refine;         /* largest number of FP64 residual evaluations of a pair */
     int failed_pair;        /* index of the first failed pair, or -1 */
     long long total_refine; /* FP64 residual evaluations summed over pairs */
+    double p_int;           /* EXX contribution to the internal pressure, Tr Pi_xx^pot / 3,  */
+                            /* Ha/bohr^3 (Eq. pxx_working; Eq. liq_press in EXX_STRESS_CUBIC) */
+    int n_warm;             /* pairs that started from a previous solution (warm_start)      */
 } exx_result;
 
 typedef struct {

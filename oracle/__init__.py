@@ -65,7 +65,7 @@ class Params(C.Structure):
 
 
 def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, tol=1e-10, fd_n=3, lmax=6,
-                max_iter=20000, nq=15, n_threads=0, lattice0=None) -> Params:
+                max_iter=20000, nq=15, n_threads=0, lattice0=None, freeze_aux=False) -> Params:
     p = Params()
     p.r_pair = r_pair
     p.r_pe_pair = r_pe
@@ -79,7 +79,8 @@ def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, 
     p.nq = nq
     p.n_threads = n_threads
     if lattice0 is not None:
-        p.frozen = 1
+        # offsets of lattice0; aux directions of the current cell unless freeze_aux
+        p.frozen = 2 if freeze_aux else 1
         for k, v in enumerate(np.asarray(lattice0, float).ravel()):
             p.lattice0[k] = float(v)
     return p

@@ -51,7 +51,9 @@ typedef struct {
     double r_pair, r_pe_self, r_pe_pair, r_me_self, r_me_pair;
     double cg_tol;
     int fd_n, lmax, cg_max_iter, nq, n_threads;
-    int frozen;             /* 1: offsets and aux directions come from lattice0 */
+    int frozen;             /* 1: offsets come from lattice0 (Sec. III B 2) and the aux directions are
+                               chosen for the current cell, as Algorithm 1 runs at every MD step
+                               (Sec. III C); 2: the aux directions of lattice0 are kept as well */
     double lattice0[9];     /* rows = lattice vectors of the reference cell */
 } orc_params;
 
@@ -462,8 +464,8 @@ static int build_stencil(const orc_cell *c, int n, int nq, const int (*aux_fixed
 
 static int stencil_for(const orc_cell *cell, const orc_params *P, const orc_cell *cell0, orc_stencil *st)
 {
-    if (!P->frozen) return build_stencil(cell, P->fd_n, P->nq, NULL, 0, st);
-    /* frozen: directions from the reference cell, coefficients from the current one */
+    if (P->frozen != 2) return build_stencil(cell, P->fd_n, P->nq, NULL, 0, st);
+    /* aux directions frozen too: directions from the reference cell, coefficients from the current one */
     orc_stencil st0;
     int e = build_stencil(cell0, P->fd_n, P->nq, NULL, 0, &st0);
     if (e) return e;

@@ -113,6 +113,15 @@ struct exx_plan {
     int pairs_cap = 0;
     int last_count = 0;
     PairOut *d_out = nullptr;
+    // warm start (params.warm_start): solutions of the last solve, one FP32 vector per pair
+    int32_t *d_inv[2] = {};           // dense-box offset -> PE index of each set
+    int32_t *d_warm_map = nullptr;    // [max_orb][max_orb] pair index of (i, j) in d_pairs, -1 none
+    float *d_warm_v[2] = {};          // solution stores; d_warm_v[warm_cur] holds the last solve's
+    int warm_cap = 0;                 // pairs each store holds
+    long long warm_stride = 0;        // floats per pair (largest N_PE of the two sets)
+    int warm_cur = 0;
+    int warm_n = 0;                   // valid pairs in d_warm_v[warm_cur]; 0: next solve starts cold
+    int warm_norb = -1;
 };
 
 static bool same_cell(const exx_cell &a, const exx_cell &b)
@@ -128,7 +137,23 @@ static int check_params(const exx_params *p)
     if (p->lmax < 0 || p->lmax > kMaxL) return EXX_ERR_ARG;
     if (!(p->r_pair >= 0.0) || !(p->cg_tol > 0.0) || p->cg_max_iter < 1 || p->nq < 1) return EXX_ERR_ARG;
     if (p->precision != EXX_FP64 && p->precision != EXX_MIXED) return EXX_ERR_ARG;
+    if (p->stress_mode < EXX_STRESS_FULL || p->stress_mode > EXX_STRESS_CUBIC) return EXX_ERR_ARG;
+    if (p->warm_start != 0 && p->warm_start != 1) return EXX_ERR_ARG;
+    if (p->frozen < 0 || p->frozen > 2) return EXX_ERR_ARG;
     return EXX_OK;
+}
+
+// lattice = L I (simple cubic), the precondition of the EXX_STRESS_CUBIC shortcut
+static bool simple_cubic(const exx_cell &c)
+{
+    const double L = c.lattice[0][0];
+    if (!(L > 0.0)) return false;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double want = a == b ? L : 0.0;
+            if (std::fabs(c.lattice[a][b] - want) > 1e-12 * L) return false;
+        }
+    return true;
 }
 
 static void free_geometry(exx_plan *p)
@@ -139,12 +164,52 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_sh_m[s]);
         dev_free(p->d_halo_off[s]);
         dev_free(p->d_groups[s]);
+        dev_free(p->d_inv[s]);
         dev_free(p->d_S64[s]);
         dev_free(p->d_T64[s]);
         dev_free(p->d_S32[s]);
         dev_free(p->d_T32[s]);
     }
     p->tables_valid = false;
+    p->warm_n = 0;   // the offsets change: stored solutions no longer apply
+}
+
+// Offsets, stencil and layout for cell0 (and the aux directions to freeze).
+// Dense CG layouts of both offset sets for the plan's current stencil (box
+// margins, strides, groups and halo order depend on the stencil directions),
+// uploaded to the device.
+static int upload_layouts(exx_plan *p)
+{
+    for (int s = 0; s < 2; ++s) {
+        SetLayout L;
+        int e = make_layout(p->off[s], p->stencil, p->params.fd_order, L);
+        if (e) return e;
+        dev_free(p->d_pe_m[s]);
+        dev_free(p->d_pe_off[s]);
+        dev_free(p->d_sh_m[s]);
+        dev_free(p->d_halo_off[s]);
+        dev_free(p->d_groups[s]);
+        dev_free(p->d_inv[s]);
+        if ((e = dev_alloc(&p->d_pe_m[s], L.n_pe)) || (e = dev_alloc(&p->d_pe_off[s], L.n_pe)) ||
+            (e = dev_alloc(&p->d_sh_m[s], L.n_shell)) || (e = dev_alloc(&p->d_halo_off[s], L.n_halo)) ||
+            (e = dev_alloc(&p->d_groups[s], L.groups.size())))
+            return e;
+        CK(cudaMemcpy(p->d_pe_m[s], L.pe_m.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->d_pe_off[s], L.pe_off.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
+        if (L.n_shell) CK(cudaMemcpy(p->d_sh_m[s], L.sh_m.data(), 4 * L.n_shell, cudaMemcpyHostToDevice));
+        if (L.n_halo) CK(cudaMemcpy(p->d_halo_off[s], L.halo_off.data(), 4 * L.n_halo, cudaMemcpyHostToDevice));
+        if (!L.groups.empty())
+            CK(cudaMemcpy(p->d_groups[s], L.groups.data(), 4 * L.groups.size(), cudaMemcpyHostToDevice));
+        if (p->params.warm_start) {
+            std::vector<int32_t> inv((size_t)L.box, -1);
+            for (int q = 0; q < L.n_pe; ++q) inv[(size_t)L.pe_off[q]] = q;
+            if ((e = dev_alloc(&p->d_inv[s], inv.size()))) return e;
+            CK(cudaMemcpy(p->d_inv[s], inv.data(), 4 * inv.size(), cudaMemcpyHostToDevice));
+        }
+        p->lay[s] = std::move(L);
+    }
+    p->tables_valid = false;   // the shell order (halo first) may have changed
+    return EXX_OK;
 }
 
 // Offsets, stencil and layout for cell0 (and the aux directions to freeze).
@@ -163,48 +228,60 @@ static int build_geometry(exx_plan *p)
     for (int s = 0; s < 2; ++s) {
         e = make_offsets(p->metric, rpe[s], rme[s], p->off[s]);
         if (e) return e;
-        e = make_layout(p->off[s], p->stencil, p->params.fd_order, p->lay[s]);
-        if (e) return e;
-        const SetLayout &L = p->lay[s];
-        if ((e = dev_alloc(&p->d_pe_m[s], L.n_pe)) || (e = dev_alloc(&p->d_pe_off[s], L.n_pe)) ||
-            (e = dev_alloc(&p->d_sh_m[s], L.n_shell)) || (e = dev_alloc(&p->d_halo_off[s], L.n_halo)) ||
-            (e = dev_alloc(&p->d_groups[s], L.groups.size())) ||
-            (e = dev_alloc(&p->d_S64[s], (size_t)L.n_pe * kNlm)) ||
-            (e = dev_alloc(&p->d_S32[s], (size_t)L.n_pe * kNlm)) ||
-            (e = dev_alloc(&p->d_T64[s], (size_t)L.n_shell * kNlm)) ||
-            (e = dev_alloc(&p->d_T32[s], (size_t)L.n_shell * kNlm)))
+        const OffsetSet &o = p->off[s];
+        if ((e = dev_alloc(&p->d_S64[s], (size_t)o.n_pe * kNlm)) ||
+            (e = dev_alloc(&p->d_S32[s], (size_t)o.n_pe * kNlm)) ||
+            (e = dev_alloc(&p->d_T64[s], (size_t)(o.n_me - o.n_pe) * kNlm)) ||
+            (e = dev_alloc(&p->d_T32[s], (size_t)(o.n_me - o.n_pe) * kNlm)))
             return e;
-        CK(cudaMemcpy(p->d_pe_m[s], L.pe_m.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(p->d_pe_off[s], L.pe_off.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
-        if (L.n_shell) CK(cudaMemcpy(p->d_sh_m[s], L.sh_m.data(), 4 * L.n_shell, cudaMemcpyHostToDevice));
-        if (L.n_halo) CK(cudaMemcpy(p->d_halo_off[s], L.halo_off.data(), 4 * L.n_halo, cudaMemcpyHostToDevice));
-        if (!L.groups.empty())
-            CK(cudaMemcpy(p->d_groups[s], L.groups.data(), 4 * L.groups.size(), cudaMemcpyHostToDevice));
     }
+    if ((e = upload_layouts(p))) return e;
     p->cell = p->cell0;
     p->tables_valid = false;
     return EXX_OK;
 }
 
-// Metric and stencil coefficients for the current cell, offsets held fixed.
+static bool same_directions(const Stencil &a, const Stencil &b)
+{
+    if (a.ndir != b.ndir) return false;
+    for (int d = 0; d < a.ndir; ++d)
+        for (int k = 0; k < 3; ++k)
+            if (a.dir[d][k] != b.dir[d][k]) return false;
+    return true;
+}
+
+// Metric and stencil for the current cell with the offsets held fixed
+// (Sec. III B 2).  frozen = 1: the aux directions are chosen for the current
+// cell, as Algorithm 1 runs at the beginning of every MD step (Sec. III C);
+// frozen = 2: the plan cell's aux directions are kept as well.  When the
+// directions change, the dense layouts are rebuilt from the same offsets (the
+// halo check runs again there).
 static int update_metric(exx_plan *p, const exx_cell &cell)
 {
     Metric m;
     int e = make_metric(cell.lattice, cell.n, m);
     if (e) return e;
     Stencil st;
-    e = make_stencil(m, p->params.fd_order, p->params.nq, p->n_aux ? p->aux : nullptr, p->n_aux, st);
+    static const int kNoAux[3][3] = {};
+    if (p->params.frozen == 2)
+        e = make_stencil(m, p->params.fd_order, p->params.nq, p->n_aux ? p->aux : kNoAux, p->n_aux, st);
+    else
+        e = make_stencil(m, p->params.fd_order, p->params.nq, nullptr, 0, st);
     if (e) return e;
-    // the frozen directions keep the layout; re-check the halo for safety
-    for (int s = 0; s < 2; ++s) {
-        SetLayout L;
-        e = make_layout(p->off[s], st, p->params.fd_order, L);
-        if (e) return e;
+    const bool relayout = !same_directions(st, p->stencil);
+    if (!relayout) {
+        // same directions: the layout stands; re-check the halo for safety
+        for (int s = 0; s < 2; ++s) {
+            SetLayout L;
+            e = make_layout(p->off[s], st, p->params.fd_order, L);
+            if (e) return e;
+        }
     }
     p->metric = m;
     p->stencil = st;
     p->cell = cell;
     p->tables_valid = false;
+    if (relayout && (e = upload_layouts(p))) return e;
     return EXX_OK;
 }
 
@@ -242,6 +319,7 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
     C.max_iter = p->params.cg_max_iter;
     C.precision = p->params.precision;
     C.r_pair2 = p->params.r_pair * p->params.r_pair;
+    C.stress_mode = p->params.stress_mode;
     for (int s = 0; s < 2; ++s) {
         const SetLayout &L = p->lay[s];
         SetDev &S = C.set[s];
@@ -502,6 +580,9 @@ void exx_plan_destroy(exx_plan *p)
     dev_free(p->d_dbox_lo);
     dev_free(p->d_pairs);
     dev_free(p->d_out);
+    dev_free(p->d_warm_map);
+    dev_free(p->d_warm_v[0]);
+    dev_free(p->d_warm_v[1]);
     delete p;
 }
 
@@ -590,6 +671,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
         for (int a = 0; a < 3; ++a)
             if (o.box[a] != p->box[a] || cells[c].n[a] != p->cell0.n[a]) return EXX_ERR_ARG;
         if (res[c].dxx && !res[c].dbox_lo) return EXX_ERR_ARG;
+        if (p->params.stress_mode == EXX_STRESS_CUBIC && !simple_cubic(cells[c])) return EXX_ERR_ARG;
         if (res[c].dxx)
             for (int a = 0; a < 3; ++a)
                 if (res[c].dbox[a] < 1 || res[c].dbox[a] > cells[c].n[a]) return EXX_ERR_ARG;
@@ -643,6 +725,26 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
         C.row_base = row_base;
         C.cell_index = c;
         row_base += o.n_orb;
+        if (p->params.warm_start) {
+            if (p->warm_norb != o.n_orb) {
+                p->warm_n = 0;
+                p->warm_norb = o.n_orb;
+            }
+            if (!p->d_warm_map && p->max_orb > 0) {
+                if ((e = dev_alloc(&p->d_warm_map, (size_t)p->max_orb * p->max_orb))) return e;
+                CK(cudaMemsetAsync(p->d_warm_map, 0xff, 4 * (size_t)p->max_orb * p->max_orb, stream));
+            }
+            p->warm_stride = std::max(p->lay[0].n_pe, p->lay[1].n_pe);
+            if (p->warm_n > 0) {
+                C.warm_map = p->d_warm_map;
+                C.warm_rows = p->d_pairs;
+                C.warm_prev = p->d_warm_v[p->warm_cur];
+            }
+            C.warm_next = p->d_warm_v[1 - p->warm_cur];
+            C.warm_cap = C.warm_next ? p->warm_cap : 0;
+            for (int s2 = 0; s2 < 2; ++s2) C.warm_inv[s2] = p->d_inv[s2];
+            C.warm_stride = p->warm_stride;
+        }
         const size_t bsz = (size_t)o.box[0] * o.box[1] * o.box[2];
         if (o.mem == EXX_MEM_HOST && o.n_orb > 0) {
             if (!p->d_phi) {
@@ -696,6 +798,43 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], stream));
     CK(launch_pair_list(ctx->d_cells, n_cells, rows, ctx->list, stream));
+    // warm start: the solution stores must hold this solve's pairs (count read back once)
+    bool any_warm = false;
+    for (int c = 0; c < n_cells; ++c) any_warm |= plans[c]->params.warm_start != 0;
+    if (any_warm) {
+        int cnt_now[64];
+        CK(cudaMemcpyAsync(cnt_now, ctx->list.cell_count, 4 * n_cells, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        bool reupload = false;
+        for (int qi = 0; qi < n_cells; ++qi) {
+            exx_plan *p = plans[order[qi]];
+            if (!p->params.warm_start || cnt_now[qi] <= p->warm_cap) continue;
+            const int cap = (int)std::min<long long>((long long)cnt_now[qi] * 5 / 4 + 64, p->pairs_cap);
+            float *nv[2] = {nullptr, nullptr};
+            if ((e = dev_alloc(&nv[0], (size_t)cap * p->warm_stride)) ||
+                (e = dev_alloc(&nv[1], (size_t)cap * p->warm_stride))) {
+                dev_free(nv[0]);
+                return e;
+            }
+            if (p->warm_n > 0)
+                CK(cudaMemcpyAsync(nv[0], p->d_warm_v[p->warm_cur], 4 * (size_t)p->warm_n * p->warm_stride,
+                                   cudaMemcpyDeviceToDevice, stream));
+            CK(cudaStreamSynchronize(stream));
+            dev_free(p->d_warm_v[0]);
+            dev_free(p->d_warm_v[1]);
+            p->d_warm_v[0] = nv[0];
+            p->d_warm_v[1] = nv[1];
+            p->warm_cur = 0;
+            p->warm_cap = cap;
+            CellDev &C = ctx->h_cells[qi];
+            C.warm_prev = p->warm_n > 0 ? p->d_warm_v[0] : nullptr;
+            C.warm_next = p->d_warm_v[1];
+            C.warm_cap = cap;
+            reupload = true;
+        }
+        if (reupload)
+            CK(cudaMemcpyAsync(ctx->d_cells, ctx->h_cells, sizeof(CellDev) * n_cells, cudaMemcpyHostToDevice, stream));
+    }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], stream));
     const bool mixed = prec == EXX_MIXED;
     CK(launch_solve(ctx->d_cells, ctx->list, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
@@ -738,6 +877,18 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
         r.max_refine = cr.max_refine;
         r.total_refine = cr.total_refine;
         r.failed_pair = cr.failed_pair;
+        r.n_warm = cr.pad;
+        r.p_int = (r.stress[0][0] + r.stress[1][1] + r.stress[2][2]) / 3.0;
+        if (p->params.stress_mode == EXX_STRESS_CUBIC) {
+            // Eqs. liq_press, dexxdL: p_int = E_xx / (3V), Tr sigma = -E_xx / L
+            const double L = cells[c].lattice[0][0];
+            r.p_int = r.e_xx / (3.0 * L * L * L);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) r.dedh[a][b] = a == b ? -r.e_xx / (3.0 * L) : 0.0;
+        }
+        if (p->params.stress_mode != EXX_STRESS_FULL)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) r.stress[a][b] = a == b ? r.p_int : 0.0;
         // keep this cell's pair list and per-pair outputs with the plan
         p->last_count = std::min(cnt, p->pairs_cap);
         if (p->last_count) {
@@ -745,6 +896,13 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
                                cudaMemcpyDeviceToDevice, stream));
             CK(cudaMemcpyAsync(p->d_out, ctx->list.out + h_start[qi], sizeof(PairOut) * p->last_count,
                                cudaMemcpyDeviceToDevice, stream));
+        }
+        if (p->params.warm_start && p->d_warm_map) {
+            // the solutions just stored become the guesses of the next solve; index them by (i, j)
+            p->warm_cur = 1 - p->warm_cur;
+            p->warm_n = std::min(p->last_count, p->warm_cap);
+            CK(cudaMemsetAsync(p->d_warm_map, 0xff, 4 * (size_t)p->max_orb * p->max_orb, stream));
+            if (p->warm_n > 0) CK(launch_warm_map(p->d_pairs, p->warm_n, orbs[c].n_orb, p->d_warm_map, stream));
         }
         if (r.dxx && r.mem == EXX_MEM_HOST) {
             const size_t dsz = (size_t)r.dbox[0] * r.dbox[1] * r.dbox[2] * orbs[c].n_orb;

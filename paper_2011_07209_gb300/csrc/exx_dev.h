@@ -27,6 +27,15 @@ struct SetDev {
     const float *T32;
 };
 
+// One unique pair (i <= j): lattice image k of j and grid-resolved centre g.
+struct PairRec {
+    int i, j;
+    int k[3];
+    int g[3];
+    int cell;
+    int pad;
+};
+
 // Everything a pair of one cell needs; one per cell, in device memory.
 struct CellDev {
     double h[3][3], hinv[3][3], J[3][3];
@@ -54,16 +63,17 @@ struct CellDev {
     // rows of the pair list of this cell: global row index base
     int row_base;
     int cell_index;
+    int stress_mode;               // 2: simple-cubic shortcut, the sigma integrals are skipped
+    // warm start: initial guesses from the previous solve of the same plan
+    const int32_t *warm_map;       // [n_orb][n_orb] index of pair (i, j) in warm_rows, -1 none; NULL: cold
+    const PairRec *warm_rows;
+    const float *warm_prev;        // [..][warm_stride] previous solutions on PE (PE order of the set)
+    float *warm_next;              // [warm_cap][warm_stride] solutions of this solve, or NULL
+    const int32_t *warm_inv[2];    // [box] dense-box offset -> PE index of each set, -1 outside PE
+    long long warm_stride;
+    int warm_cap;
 };
 
-// One unique pair (i <= j): lattice image k of j and grid-resolved centre g.
-struct PairRec {
-    int i, j;
-    int k[3];
-    int g[3];
-    int cell;
-    int pad;
-};
 
 // Per-pair outputs (indexed by the global pair index).
 struct PairOut {
@@ -87,7 +97,7 @@ struct CellResult {
     int failed_pair;
     int max_iter;
     int max_refine;
-    int pad;
+    int pad;           // n_warm: pairs that started from a previous solution
 };
 
 // Pair-list bookkeeping in device memory.

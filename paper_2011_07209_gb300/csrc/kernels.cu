@@ -453,6 +453,7 @@ struct CgMixed {
     double *red;
     int ndir, fdn, max_iter;
     double stop, bn, inner_red;
+    double r0n;   // norm of the starting residual b - A v0 (the first frame)
 };
 
 __device__ __noinline__ void cg_mixed(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
@@ -483,8 +484,8 @@ __device__ __noinline__ void cg_mixed(const CgMixed &cg, int &iters, int &refine
             const int32_t *__restrict__ poff = S.pe_off;
             const int npe = S.n_pe;
             constexpr int U = EXX_UNROLL;
-            if (bn > 0.0) {
-                double S_ = bn;
+            if (bn > 0.0 && cg.r0n > stop) {
+                double S_ = cg.r0n;
                 double rr;
                 {
                     double a0[1];
@@ -776,12 +777,12 @@ __device__ __noinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &
         }
     }
 
-    double S_ = cg.bn;
+    if (!(cg.r0n > stop)) return;   // the starting guess already meets the tolerance
     double rr;
     {
         double a0[1];
         DF a = {0.f, 0.f};
-        const double sc = 1.0 / S_;
+        const double sc = 1.0 / cg.r0n;
         for (int k = tid; k < npe; k += nt) {
             const int off = poff[k];
             const float r = (float)(r64[k] * sc);
@@ -803,7 +804,7 @@ __device__ __noinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &
     if (tid == 0) {
         cs.rr = rr;
         cs.rmax = sqrt(rr);
-        cs.S = cg.bn;
+        cs.S = cg.r0n;
     }
     __syncthreads();
     float2 *red2 = reinterpret_cast<float2 *>(red);
@@ -1025,11 +1026,49 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         __syncthreads();
 
         // ---- Step IV: Poisson solve (Eq. pe) ----
+        // b = 4 pi rho + (Dirichlet terms): the residual of v = 0 on PE
         double rr2 = residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red);
         const double bn = sqrt(rr2);
         const double stop = C.tol * bn;
         int iters = 0, refine = 1, status = 0;
         double rnorm = bn;
+        // warm start: this pair's solution of the previous solve, moved by the
+        // change of the grid-resolved centre, as the starting guess
+        int warm = -1;
+        int dg[3] = {0, 0, 0};
+        if (C.warm_map && bn > 0.0) {
+            const int o = C.warm_map[(size_t)pr.i * C.n_orb + pr.j];
+            if (o >= 0) {
+                const PairRec q = C.warm_rows[o];
+                if (q.i == pr.i && q.j == pr.j && q.k[0] == pr.k[0] && q.k[1] == pr.k[1] && q.k[2] == pr.k[2]) {
+                    warm = o;
+                    for (int a = 0; a < 3; ++a) {
+                        int d = wrapi(pr.g[a] - q.g[a], C.n[a]);
+                        if (2 * d >= C.n[a]) d -= C.n[a];
+                        dg[a] = d;
+                    }
+                }
+            }
+        }
+        if (warm >= 0) {
+            const int32_t *inv = C.warm_inv[self ? 0 : 1];
+            const float *src = C.warm_prev + (size_t)warm * C.warm_stride;
+            for (int k = tid; k < S.n_pe; k += nt) {
+                int m0, m1, m2;
+                unpack_m(S.pe_m[k], m0, m1, m2);
+                const int u0 = m0 + dg[0] + S.c[0], u1 = m1 + dg[1] + S.c[1], u2 = m2 + dg[2] + S.c[2];
+                double v = 0.0;
+                if (u0 >= 0 && u0 < S.B[0] && u1 >= 0 && u1 < S.B[1] && u2 >= 0 && u2 < S.B[2]) {
+                    const int kk = inv[((size_t)u0 * S.B[1] + u1) * S.B[2] + u2];
+                    if (kk >= 0) v = (double)src[kk];
+                }
+                vbox[S.pe_off[k]] = v;
+            }
+            __syncthreads();
+            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            rr2 = rnorm * rnorm;
+            ++refine;
+        }
         if (!mixed) {
             // plain FP64 CG: x in vbox (PE), r in r64, p in pbox, q in qv
             double *pd = (double *)pbox;
@@ -1096,6 +1135,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             cg.max_iter = C.max_iter;
             cg.stop = stop;
             cg.bn = bn;
+            cg.r0n = rnorm;
             cg.inner_red = inner_red;
             if ((S.n_groups + kSweepChunkGroups * nt - 1) / (kSweepChunkGroups * nt) <= kMaxSweepChunks) {
                 switch (fdn) {
@@ -1110,15 +1150,26 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             }
         }
 
+        // keep this pair's solution for the next warm-started solve
+        if (C.warm_next) {
+            const int tl = t - L.cell_start[pr.cell];
+            if (tl >= 0 && tl < C.warm_cap) {
+                float *dst = C.warm_next + (size_t)tl * C.warm_stride;
+                for (int k = tid; k < S.n_pe; k += nt) dst[k] = (float)vbox[S.pe_off[k]];
+            }
+        }
+
         // ---- Step V: energy and stress integrals (Eqs. exxGen_mlwf, sxx_working, d1_1) ----
         double acc[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+        const bool want_sigma = C.stress_mode != 2;
         for (int k = tid; k < S.n_pe; k += nt) {
             const int off = S.pe_off[k];
             const double rk = rho[k];
             const double v = vbox[off];
             acc[0] += rk * v;
+            if (!want_sigma) continue;
             double dxi[3];
 #pragma unroll
             for (int al = 0; al < 3; ++al) {
@@ -1199,7 +1250,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             o.iters = iters;
             o.refine = refine;
             o.status = status ? status : (s_flag ? 7 : 0);
-            o.pad = 0;
+            o.pad = warm >= 0 ? 1 : 0;   // started from a previous solution
             L.out[t] = o;
         }
         (void)rnorm;
@@ -1212,9 +1263,10 @@ __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ ce
     const int c = blockIdx.x;
     const CellDev &C = cells[c];
     __shared__ double red[33 * 10 + 64];
-    __shared__ int s_fail, s_status, s_maxit, s_maxref;
+    __shared__ int s_fail, s_status, s_maxit, s_maxref, s_warm;
     __shared__ unsigned long long s_tot, s_tref;
     if (threadIdx.x == 0) {
+        s_warm = 0;
         s_fail = 0x7fffffff;
         s_status = 0;
         s_maxit = 0;
@@ -1231,7 +1283,7 @@ __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ ce
     const int per = (cnt + blockDim.x - 1) / blockDim.x;
     const int p0 = threadIdx.x * per, p1 = min(cnt, p0 + per);
     long long tot = 0, tref = 0;
-    int maxit = 0, maxref = 0, fail = 0x7fffffff, status = 0;
+    int maxit = 0, maxref = 0, fail = 0x7fffffff, status = 0, nwarm = 0;
     for (int p = p0; p < p1; ++p) {
         const PairRec pr = L.pairs[start + p];
         const PairOut o = L.out[start + p];
@@ -1240,6 +1292,7 @@ __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ ce
         for (int k = 0; k < 9; ++k) acc[1 + k] += w * o.sig[k];
         tot += o.iters;
         tref += o.refine;
+        nwarm += o.pad;
         maxit = max(maxit, o.iters);
         maxref = max(maxref, o.refine);
         if (o.status && p < fail) {
@@ -1253,6 +1306,7 @@ __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ ce
     atomicAdd(&s_tot, (unsigned long long)tot);
     atomicAdd(&s_tref, (unsigned long long)tref);
     atomicMin(&s_fail, fail);
+    atomicAdd(&s_warm, nwarm);
     __syncthreads();
     if (fail == s_fail && fail != 0x7fffffff) s_status = status;
     __syncthreads();
@@ -1273,7 +1327,7 @@ __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ ce
         r.failed_pair = (s_fail == 0x7fffffff) ? -1 : s_fail;
         r.max_iter = s_maxit;
         r.max_refine = s_maxref;
-        r.pad = 0;
+        r.pad = s_warm;   // pairs that started from a previous solution
         res[c] = r;
     }
 }
@@ -1313,6 +1367,23 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
     W.off_e = slots.off_e;
     if (mixed) k_pair_solve<float><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     else k_pair_solve<double><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
+    return cudaGetLastError();
+}
+
+// map[i n_orb + j] = t for the pairs t of a cell's list (the warm-start index)
+__global__ void k_warm_map(const PairRec *__restrict__ rows, int n, int n_orb, int *__restrict__ map)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const PairRec r = rows[t];
+        if (r.i >= 0 && r.j >= 0 && r.i < n_orb && r.j < n_orb) map[(size_t)r.i * n_orb + r.j] = t;
+    }
+}
+
+cudaError_t launch_warm_map(const PairRec *rows, int n, int n_orb, int *map, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_warm_map<<<(n + 255) / 256, 256, 0, s>>>(rows, n, n_orb, map);
     return cudaGetLastError();
 }
 

@@ -31,5 +31,6 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
                          int inner_shift, cudaStream_t s);
 cudaError_t launch_finalize(const CellDev *cells, int n_cells, const ListDev &L, CellResult *res, cudaStream_t s);
 int solve_blocks_per_sm(bool mixed);
+cudaError_t launch_warm_map(const PairRec *rows, int n, int n_orb, int *map, cudaStream_t s);
 
 }  // namespace exx

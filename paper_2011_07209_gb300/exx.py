@@ -19,6 +19,7 @@ from . import build as _build
 OK, ERR_ARG, ERR_CELL, ERR_HALO, ERR_NK, ERR_CG, ERR_CAPACITY, ERR_BOX, ERR_OOM, ERR_CUDA = range(10)
 FP64, MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
+STRESS_FULL, STRESS_ISOTROPIC, STRESS_CUBIC = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()
@@ -37,7 +38,7 @@ class Params(C.Structure):
     _fields_ = [("r_pair", C.c_double), ("r_pe_self", C.c_double), ("r_pe_pair", C.c_double),
                 ("r_me_self", C.c_double), ("r_me_pair", C.c_double), ("cg_tol", C.c_double),
                 ("fd_order", C.c_int), ("lmax", C.c_int), ("cg_max_iter", C.c_int), ("nq", C.c_int),
-                ("precision", C.c_int), ("frozen", C.c_int)]
+                ("precision", C.c_int), ("frozen", C.c_int), ("stress_mode", C.c_int), ("warm_start", C.c_int)]
 
 
 class Orbitals(C.Structure):
@@ -51,7 +52,7 @@ class Result(C.Structure):
                 ("e_xx", C.c_double), ("dedh", C.c_double * 9), ("stress", C.c_double * 9),
                 ("n_pairs", C.c_int), ("n_aux", C.c_int), ("n_stcl", C.c_int), ("max_cg_iter", C.c_int),
                 ("total_cg_iter", C.c_longlong), ("max_refine", C.c_int), ("failed_pair", C.c_int),
-                ("total_refine", C.c_longlong)]
+                ("total_refine", C.c_longlong), ("p_int", C.c_double), ("n_warm", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -126,7 +127,7 @@ def make_cell(lattice, n) -> Cell:
 
 
 def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, tol=1e-9, fd_order=3, lmax=6,
-                max_iter=20000, nq=15, precision=MIXED, frozen=False) -> Params:
+                max_iter=20000, nq=15, precision=MIXED, frozen=False, stress_mode=0, warm_start=False) -> Params:
     p = Params()
     p.r_pair = r_pair
     p.r_pe_pair = r_pe
@@ -139,7 +140,9 @@ def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, 
     p.cg_max_iter = max_iter
     p.nq = nq
     p.precision = precision
-    p.frozen = int(bool(frozen))
+    p.frozen = int(frozen)   # 0, 1 (offsets frozen) or 2 (offsets and aux directions frozen)
+    p.stress_mode = int(stress_mode)
+    p.warm_start = int(bool(warm_start))
     return p
 
 
@@ -299,7 +302,8 @@ def result_dict(r: Result) -> dict:
     return {"e_xx": r.e_xx, "dedh": np.array(list(r.dedh)).reshape(3, 3),
             "stress": np.array(list(r.stress)).reshape(3, 3), "n_pairs": r.n_pairs, "n_aux": r.n_aux,
             "n_stcl": r.n_stcl, "max_cg_iter": r.max_cg_iter, "total_cg_iter": r.total_cg_iter,
-            "max_refine": r.max_refine, "failed_pair": r.failed_pair, "total_refine": r.total_refine}
+            "max_refine": r.max_refine, "failed_pair": r.failed_pair, "total_refine": r.total_refine,
+            "p_int": r.p_int, "n_warm": r.n_warm}
 
 
 def pair_list_noalloc(lattice, n, centres, n_orb, r_pair, rows, n_pairs, stream=None) -> int:

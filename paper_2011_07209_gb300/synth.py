@@ -54,6 +54,16 @@ class MLWFSet:
     def n_orb(self) -> int:
         return int(self.centres.shape[0])
 
+    def padded(self, box) -> "MLWFSet":
+        """The same orbitals on larger boxes (zeros appended after each box's last point)."""
+        box = np.asarray(box, np.int32)
+        assert np.all(box >= self.box)
+        phi = np.zeros((self.n_orb,) + tuple(int(b) for b in box))
+        b0, b1, b2 = (int(b) for b in self.box)
+        phi[:, :b0, :b1, :b2] = self.phi
+        return MLWFSet(lattice=self.lattice, n=self.n, centres=self.centres, a=self.a, box=box,
+                       box_lo=self.box_lo, phi=phi, s=self.s)
+
     def subset(self, k: int) -> "MLWFSet":
         """The first k orbitals of the cell (same grid and boxes)."""
         return MLWFSet(lattice=self.lattice, n=self.n, centres=self.centres[:k].copy(), a=self.a[:k].copy(),

@@ -51,8 +51,8 @@ def _gpu(ctx, ws, r_pair, r_pe, r_me, tol, precision, frozen=False, lattice0=Non
     return out
 
 
-def _oracle(ws, r_pair, r_pe, r_me, tol, dbox, dbox_lo, sel=None, lattice0=None):
-    p = oracle.make_params(r_pair=r_pair, r_pe=r_pe, r_me=r_me, tol=tol, lattice0=lattice0)
+def _oracle(ws, r_pair, r_pe, r_me, tol, dbox, dbox_lo, sel=None, lattice0=None, freeze_aux=False):
+    p = oracle.make_params(r_pair=r_pair, r_pe=r_pe, r_me=r_me, tol=tol, lattice0=lattice0, freeze_aux=freeze_aux)
     return oracle.exx(ws, p, sel=sel, dbox=dbox, dbox_lo=dbox_lo, want_d=sel is None)
 
 
@@ -107,6 +107,30 @@ def test_frozen_strained_cell(ctx):
     eps = np.array([[2e-3, 1e-3, 0], [1e-3, -1e-3, 5e-4], [0, 5e-4, 1e-3]])
     ws = synth.strained(ws0, eps)
     g = _gpu(ctx, ws, 7.0, 5.0, 6.5, 1e-10, "fp64", frozen=True, lattice0=lat0)
+    o = _oracle(ws, 7.0, 5.0, 6.5, 1e-10, g["dbox"], g["dbox_lo"], lattice0=lat0)
+    _compare(g, o, "fp64")
+
+
+def test_frozen_aux_directions(ctx):
+    # frozen = 2: the plan cell's aux directions are kept under strain as well
+    lat0 = 14.0 * np.array([[1.0, 0, 0], [0.1, 1.0, 0], [0.05, -0.08, 1.0]])
+    ws0 = synth.water_cell(lat0, (56, 56, 56), 3, 5)
+    eps = np.array([[-1e-3, 5e-4, 2e-4], [5e-4, 2e-3, 0], [2e-4, 0, -5e-4]])
+    ws = synth.strained(ws0, eps)
+    g = _gpu(ctx, ws, 7.0, 5.0, 6.5, 1e-10, "mixed", frozen=2, lattice0=lat0)
+    o = _oracle(ws, 7.0, 5.0, 6.5, 1e-10, g["dbox"], g["dbox_lo"], lattice0=lat0, freeze_aux=True)
+    _compare(g, o, "mixed")
+
+
+def test_frozen_cubic_plan_cell_under_strain(ctx):
+    # a cubic plan cell has no aux directions; a strained step needs three, chosen
+    # for that step (Algorithm 1 at every MD step) while the offsets stay frozen
+    lat0 = np.diag([12.0] * 3)
+    ws0 = synth.water_cell(lat0, (40, 40, 40), 2, 31)
+    eps = np.array([[1e-3, 4e-4, -3e-4], [4e-4, -2e-3, 6e-4], [-3e-4, 6e-4, 5e-4]])
+    ws = synth.strained(ws0, eps)
+    g = _gpu(ctx, ws, 7.0, 5.0, 6.5, 1e-10, "fp64", frozen=True, lattice0=lat0)
+    assert g["n_aux"] == 3
     o = _oracle(ws, 7.0, 5.0, 6.5, 1e-10, g["dbox"], g["dbox_lo"], lattice0=lat0)
     _compare(g, o, "fp64")
 
