@@ -320,6 +320,111 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+WORKLOADS = {
+    "triclinic128": "water128_triclinic29.6bohr_n150: 512 MLWFs, R_pair/R_PE/R_ME = 8/6/8 bohr, 37-point NK "
+                    "stencil (3 aux directions), CG tol 1e-9",
+    "batch3": "three cells in one launch: water32 cubic 18.6 (93^3), water96 26.8x26.8x28.0 (134x134x140), "
+              "water192 monoclinic 33.9 shear 0.12 (169x169x171); R_PE from {5,6,7} per cell, R_ME 8, CG tol 1e-9",
+    "trajectory256": "water256_triclinic37.3bohr_n190 trajectory: 1024 MLWFs, one MD step per step (symmetric "
+                     "strain N(0,1e-3), centres += N(0,0.05), orbitals re-sampled), frozen offsets, CG tol 1e-9",
+}
+
+
+def run_workload(args, rank, world, local_rank):
+    """The other benchmark cells (one JSON line; no e2e or CPU arm)."""
+    import numpy as np
+    import torch
+
+    import paper_2011_07209_gb300.synth as synth
+    from paper_2011_07209_gb300 import driver, exx
+
+    torch.cuda.set_device(local_rank)
+    ctx = exx.Context(local_rank)
+    prec = exx.FP64 if args.precision == "fp64" else exx.MIXED
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx.set_timing(True)
+    n_total = args.warmup + args.steps
+    if args.workload == "triclinic128":
+        c = synth.CONFIGS[3]
+        ws = synth.make_config(3)
+        p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=c["tol"], precision=prec)
+        cr = driver.prepare(ctx, ws, p)
+        step_runs = [[cr]] * n_total
+    elif args.workload == "batch3":
+        runs = []
+        for name, ws, r_pe in synth.make_batch(4):
+            p = exx.make_params(r_pair=8.0, r_pe=r_pe, r_me=8.0, tol=1e-9, precision=prec)
+            runs.append(driver.prepare(ctx, ws, p))
+        step_runs = [runs] * n_total
+    else:
+        c = synth.CONFIGS[5]
+        ws0 = synth.make_config(5)
+        steps = synth.trajectory(ws0, n_total, seed=synth.SEED_BASE + 500)
+        box = np.max([w.box for w in steps], axis=0)
+        steps = [w.padded(box) for w in steps]
+        p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=c["tol"], precision=prec, frozen=True,
+                            warm_start=not args.cold)
+        plan = exx.Plan(ctx, ws0.lattice, ws0.n, p, ws0.n_orb, box)
+        dbox = np.max([exx.dbox_layout(w.lattice, w.n, w.centres, p)[0] for w in steps], axis=0)
+        dxx = torch.zeros((ws0.n_orb,) + tuple(int(b) for b in dbox), dtype=torch.float64, device="cuda")
+        step_runs = [[driver.prepare(ctx, w, p, plan=plan, dxx=dxx)] for w in steps]
+
+    def one(runs):
+        if len(runs) == 1:
+            o = driver.run(ctx, runs[0], pair_outputs=False, stream=sh)
+            return [o], ctx.timing()["solve_ms"]
+        o = driver.run_batch(ctx, runs, stream=sh)
+        return o, ctx.timing()["solve_ms"]
+
+    for k in range(args.warmup):
+        one(step_runs[k])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(None)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    n_pairs = tot_iter = tot_ref = n_warm = 0
+    solve_ms = []
+    bytes_launch = 0.0
+    for k in range(args.warmup, n_total):
+        outs, ms = one(step_runs[k])
+        solve_ms.append(ms)
+        for o, r in zip(outs, step_runs[k]):
+            info = r.plan.info()
+            n_pairs += o["n_pairs"]
+            tot_iter += o["total_cg_iter"]
+            tot_ref += o["total_refine"]
+            n_warm += o.get("n_warm", 0)
+            bytes_launch += algorithmic_bytes(o["n_pairs"], o["total_cg_iter"], o["total_refine"], info["n_pe_pair"],
+                                              info["n_me_pair"], 8.0 if prec == exx.FP64 else 4.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    peak, peak_kind = measured_hbm()
+    avg_solve = sum(solve_ms) / len(solve_ms)
+    achieved = bytes_launch / args.steps / (avg_solve / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": n_pairs / (elapsed / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == exx.FP64 else "mixed-f32-f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_step": n_pairs / args.steps,
+                   "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_fp64_residuals": tot_ref / max(n_pairs, 1),
+                   "warm_started_pairs_per_step": n_warm / args.steps,
+                   "warm_start": args.workload == "trajectory256" and not args.cold},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_pair_solve", "avg_launch_ms": avg_solve,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
+        "clocks": clocks, "gpu_launches": 5 * args.steps, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +435,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="water64", choices=["water64"] + sorted(WORKLOADS),
+                    help="water64 is the headline workload; the others print their own line")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="for --workload other than water64")
+    ap.add_argument("--cold", action="store_true", help="trajectory256 without warm-started CG")
     ap.add_argument("--subset", type=int, default=0,
                     help="solve only the pairs of the first K MLWFs (a small case of the same cell for profiling)")
     args = ap.parse_args()
@@ -340,6 +449,11 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "water64":
+        if world > 1:
+            print(json.dumps({"error": "--workload other than water64 runs on one GPU"}))
+            return 1
+        return run_workload(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

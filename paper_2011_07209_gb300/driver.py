@@ -42,7 +42,11 @@ class CellRun:
                                self.pair_iter if pair_outputs else None)
 
 
-def prepare(ctx: exx.Context, ws, params: exx.Params, *, device=0, want_d=True, plan=None, max_orb=None) -> CellRun:
+def prepare(ctx: exx.Context, ws, params: exx.Params, *, device=0, want_d=True, plan=None, max_orb=None,
+            dxx=None) -> CellRun:
+    """Device inputs and outputs of one cell.  dxx: an existing D buffer
+    [n_orb][dbox...] to write into (shared between cells solved one after the
+    other); otherwise one is allocated when want_d."""
     import torch
     dev = torch.device("cuda", device)
     if plan is None:
@@ -50,9 +54,11 @@ def prepare(ctx: exx.Context, ws, params: exx.Params, *, device=0, want_d=True, 
     phi = torch.as_tensor(np.ascontiguousarray(ws.phi), device=dev)
     centres = torch.as_tensor(np.ascontiguousarray(ws.centres, np.float64), device=dev)
     box_lo = torch.as_tensor(np.ascontiguousarray(ws.box_lo, np.int32), device=dev)
-    dbox, dbox_lo_np = exx.dbox_layout(ws.lattice, ws.n, ws.centres, params)
-    if want_d:
-        dxx = torch.zeros((ws.n_orb,) + tuple(int(x) for x in dbox), dtype=torch.float64, device=dev)
+    dbox, dbox_lo_np = exx.dbox_layout(ws.lattice, ws.n, ws.centres, params,
+                                       dbox=None if dxx is None else tuple(dxx.shape[1:]))
+    if dxx is not None or want_d:
+        if dxx is None:
+            dxx = torch.zeros((ws.n_orb,) + tuple(int(x) for x in dbox), dtype=torch.float64, device=dev)
         dbox_lo = torch.as_tensor(dbox_lo_np, device=dev)
     else:
         dxx = None

@@ -152,11 +152,20 @@ def dbox_halfwidth(lattice, n, params: Params):
     return np.array(list(hw), np.int64)
 
 
-def dbox_layout(lattice, n, centres, params: Params):
-    """D-box extent and per-orbital first index (box around each centre's grid point)."""
+def dbox_layout(lattice, n, centres, params: Params, dbox=None):
+    """D-box extent and per-orbital first index (box around each centre's grid point).
+
+    A caller-chosen dbox (at least the required extent) can be given, e.g. to
+    share one D buffer between the steps of a trajectory."""
     n = np.asarray(n, np.int64)
     hw = dbox_halfwidth(lattice, n, params)
-    dbox = np.minimum(2 * hw + 1, n)
+    need = np.minimum(2 * hw + 1, n)
+    if dbox is None:
+        dbox = need
+    else:
+        dbox = np.asarray(dbox, np.int64)
+        if np.any(dbox < need) or np.any(dbox > n):
+            raise ValueError(f"dbox {dbox} outside [{need}, {n}]")
     hinv = np.linalg.inv(np.asarray(lattice, float).T)
     frac = np.asarray(centres, float) @ hinv.T
     frac -= np.floor(frac)
