@@ -72,6 +72,7 @@ typedef enum {
 } exx_status;
 
 enum { EXX_FP64 = 0, EXX_MIXED = 1 };          /* exx_params.precision */
+enum { EXX_SOLVER_CTA = 0, EXX_SOLVER_CLUSTER = 1 };   /* exx_ctx_set_solver */
 enum { EXX_MEM_DEVICE = 0, EXX_MEM_HOST = 1 };  /* memory kind of caller buffers */
 /* exx_params.stress_mode (Sec. II C, "Isotropic Constraints"):
  *   EXX_STRESS_FULL       sigma and the full Pi_xx^pot (Eqs. sxx_working, pixx_working);
@@ -166,8 +167,11 @@ typedef struct {
     int box_self[3], box_pair[3];    /* dense CG boxes (PE plus stencil margin) */
     long long workspace_bytes;
     int pair_capacity;      /* largest number of pairs a solve can hold */
-    int ctas;               /* persistent CTAs of the pair kernel */
+    int ctas;               /* persistent CTAs of the pair kernel (of the context's last solve) */
     int threads;            /* threads per CTA */
+    int cluster;            /* CTAs per pair: 1 (one CTA per pair) or the cluster size of the */
+                            /* cluster path, which keeps a pair's FP32 CG state in the       */
+                            /* distributed shared memory of a thread-block cluster           */
 } exx_plan_info;
 
 /* Create a context on CUDA device `device` (made current for the call). */
@@ -232,6 +236,17 @@ int exx_pair_list_noalloc(const exx_cell *cell, const double *centres, int n_orb
 /* Index half-widths of a D box that holds every contribution of the pairs of
  * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);
+
+/* Choose the persistent pair solver of the mixed-precision path (Step IV).
+ * EXX_SOLVER_CTA (default): one CTA of 1024 threads per pair, CG vectors in
+ * HBM as dense boxes.  EXX_SOLVER_CLUSTER: one thread-block cluster of 16 CTAs
+ * per pair with the pair's FP32 CG state (r, q, e and the rows of p) in the
+ * cluster's distributed shared memory; it is used for a solve only when every
+ * subdomain of every cell fits (about 200 KB per CTA: R_PE = 6 bohr at
+ * 0.2 bohr spacing fits, R_PE = 7 does not) and otherwise the CTA solver runs.
+ * Both give the same results to the CG tolerance.  The FP64 path always uses
+ * the CTA solver.  Returns EXX_ERR_ARG for an unknown solver. */
+int exx_ctx_set_solver(exx_ctx *ctx, int solver);
 
 /* Stage timing of the context's last solve, measured with CUDA events
  * recorded on the solve's stream while enabled: ms[0] solid-harmonic tables

@@ -79,6 +79,10 @@ struct exx_ctx {
     CellResult *h_res = nullptr;      // pinned
     int cells_cap = 0;
     int inner_shift = 10;
+    int solver = EXX_SOLVER_CTA;   // exx_ctx_set_solver
+    int cluster_cap = -1;     // dynamic shared memory a cluster CTA can take (bytes), -1 unknown
+    int last_path = 0;        // 0: per-CTA solver, 1: cluster solver (of the last solve)
+    int last_clusters = 0;
     bool timing = false;
     cudaEvent_t ev[5] = {};
     double ms[4] = {};
@@ -115,6 +119,10 @@ struct exx_plan {
     PairOut *d_out = nullptr;
     // warm start (params.warm_start): solutions of the last solve, one FP32 vector per pair
     int32_t *d_inv[2] = {};           // dense-box offset -> PE index of each set
+    // row partitions for the cluster path (mixed precision)
+    ClusterPart cpart[2];
+    bool cl_ok[2] = {false, false};
+    int32_t *d_cl_cta[2] = {}, *d_cl_rows[2] = {}, *d_cl_grc[2] = {}, *d_cl_pegl[2] = {};
     int32_t *d_warm_map = nullptr;    // [max_orb][max_orb] pair index of (i, j) in d_pairs, -1 none
     float *d_warm_v[2] = {};          // solution stores; d_warm_v[warm_cur] holds the last solve's
     int warm_cap = 0;                 // pairs each store holds
@@ -165,6 +173,11 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_halo_off[s]);
         dev_free(p->d_groups[s]);
         dev_free(p->d_inv[s]);
+        dev_free(p->d_cl_cta[s]);
+        dev_free(p->d_cl_rows[s]);
+        dev_free(p->d_cl_grc[s]);
+        dev_free(p->d_cl_pegl[s]);
+        p->cl_ok[s] = false;
         dev_free(p->d_S64[s]);
         dev_free(p->d_T64[s]);
         dev_free(p->d_S32[s]);
@@ -205,6 +218,24 @@ static int upload_layouts(exx_plan *p)
             for (int q = 0; q < L.n_pe; ++q) inv[(size_t)L.pe_off[q]] = q;
             if ((e = dev_alloc(&p->d_inv[s], inv.size()))) return e;
             CK(cudaMemcpy(p->d_inv[s], inv.data(), 4 * inv.size(), cudaMemcpyHostToDevice));
+        }
+        dev_free(p->d_cl_cta[s]);
+        dev_free(p->d_cl_rows[s]);
+        dev_free(p->d_cl_grc[s]);
+        dev_free(p->d_cl_pegl[s]);
+        p->cl_ok[s] = false;
+        if (p->params.precision == EXX_MIXED && p->params.fd_order <= 4 &&
+            make_cluster_part(L, p->stencil, p->params.fd_order, kClusterCTAs, p->cpart[s]) == EXX_OK) {
+            const ClusterPart &cp = p->cpart[s];
+            if ((e = dev_alloc(&p->d_cl_cta[s], cp.cta.size())) || (e = dev_alloc(&p->d_cl_rows[s], cp.rows.size())) ||
+                (e = dev_alloc(&p->d_cl_grc[s], cp.grc.size())) || (e = dev_alloc(&p->d_cl_pegl[s], cp.pe_gl.size())))
+                return e;
+            CK(cudaMemcpy(p->d_cl_cta[s], cp.cta.data(), 4 * cp.cta.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(p->d_cl_rows[s], cp.rows.data(), 4 * cp.rows.size(), cudaMemcpyHostToDevice));
+            if (!cp.grc.empty()) CK(cudaMemcpy(p->d_cl_grc[s], cp.grc.data(), 4 * cp.grc.size(), cudaMemcpyHostToDevice));
+            if (!cp.pe_gl.empty())
+                CK(cudaMemcpy(p->d_cl_pegl[s], cp.pe_gl.data(), 4 * cp.pe_gl.size(), cudaMemcpyHostToDevice));
+            p->cl_ok[s] = true;
         }
         p->lay[s] = std::move(L);
     }
@@ -343,6 +374,12 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
             S.rstride[d] = L.rstride[d];
             S.d2[d] = d < p->stencil.ndir ? p->stencil.dir[d][2] : 0;
         }
+        S.cl_cta = p->cl_ok[s] ? p->d_cl_cta[s] : nullptr;
+        S.cl_rows = p->d_cl_rows[s];
+        S.cl_grc = p->d_cl_grc[s];
+        S.cl_pe_gl = p->d_cl_pegl[s];
+        S.cl_pad = p->cpart[s].pad;
+        S.cl_row_stride = p->cpart[s].row_stride;
         S.S64 = p->d_S64[s];
         S.S32 = p->d_S32[s];
         S.T64 = p->d_T64[s];
@@ -490,7 +527,15 @@ int exx_ctx_create(exx_ctx **ctx, int device)
     c->device = device;
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (const char *s = std::getenv("EXX_INNER_SHIFT")) c->inner_shift = std::max(4, std::min(22, std::atoi(s)));
+
     *ctx = c;
+    return EXX_OK;
+}
+
+int exx_ctx_set_solver(exx_ctx *ctx, int solver)
+{
+    if (!ctx || (solver != EXX_SOLVER_CTA && solver != EXX_SOLVER_CLUSTER)) return EXX_ERR_ARG;
+    ctx->solver = solver;
     return EXX_OK;
 }
 
@@ -612,8 +657,9 @@ int exx_plan_query(const exx_plan *p, exx_plan_info *info)
     const SolveSlots &s = p->params.precision == EXX_MIXED ? c->sl_mixed : c->sl_fp64;
     info->workspace_bytes = (long long)c->slots_bytes;
     info->pair_capacity = p->pairs_cap;
-    info->ctas = s.n_slots;
+    info->ctas = c->last_path == 1 ? c->last_clusters * kClusterCTAs : s.n_slots;
     info->threads = kSolveThreads;
+    info->cluster = c->last_path == 1 ? kClusterCTAs : 1;
     return EXX_OK;
 }
 
@@ -837,7 +883,31 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], stream));
     const bool mixed = prec == EXX_MIXED;
-    CK(launch_solve(ctx->d_cells, ctx->list, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
+    // the cluster path takes the launch when every set of every cell has a row
+    // partition and its CG state fits in the cluster's shared memory
+    bool use_cluster = mixed && ctx->solver == EXX_SOLVER_CLUSTER;
+    int rowtab_words = 0, cl_p = 0, cl_g = 800;   // r, q, e regions double as the moments' scratch
+    for (int c = 0; c < n_cells && use_cluster; ++c)
+        for (int s = 0; s < 2; ++s) {
+            const exx_plan *p = plans[c];
+            if (!p->cl_ok[s]) {
+                use_cluster = false;
+                break;
+            }
+            rowtab_words = std::max(rowtab_words, p->lay[s].B[0] * p->lay[s].B[1]);
+            cl_p = std::max(cl_p, p->cpart[s].max_p_floats);
+            cl_g = std::max(cl_g, p->cpart[s].max_groups);
+        }
+    if (use_cluster) {
+        if (ctx->cluster_cap < 0) ctx->cluster_cap = cluster_capacity_bytes();
+        if (cluster_dyn_bytes(rowtab_words, cl_p, cl_g) > (size_t)ctx->cluster_cap) use_cluster = false;
+    }
+    ctx->last_path = use_cluster ? 1 : 0;
+    if (use_cluster)
+        CK(launch_solve_cluster(ctx->d_cells, ctx->list, ctx->sl_mixed, rowtab_words, cl_p, cl_g, ctx->inner_shift,
+                                &ctx->last_clusters, stream));
+    else
+        CK(launch_solve(ctx->d_cells, ctx->list, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], stream));
     CK(launch_finalize(ctx->d_cells, n_cells, ctx->list, ctx->d_res, stream));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], stream));

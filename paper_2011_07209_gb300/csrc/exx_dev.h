@@ -21,6 +21,12 @@ struct SetDev {
     int n_groups;
     int rstride[6];                // dstride without the last-axis component
     int d2[6];                     // last-axis component of each direction
+    // row partition over a cluster of CTAs (cluster path; cl_cta == NULL: not available)
+    const int32_t *cl_cta;         // [nc][8]: G0, G1, K0, K1, rows, p_floats
+    const int32_t *cl_rows;        // [B0 * B1][2]: owner rank (-2 halo-only row, -1 unused), offset of column 0
+    const int32_t *cl_grc;         // [n_groups]: row id | column << 13
+    const int32_t *cl_pe_gl;       // [n_pe]: group << 2 | lane
+    int cl_pad, cl_row_stride;
     const double *S64;             // [n_pe][kNlm] regular solid harmonics r^l Y_lm(r-bar)
     const float *S32;
     const double *T64;             // [kNlm][n_shell] 4 pi / (2l+1) r^l Y_lm / r^(2l+1)

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include <algorithm>
+
 #include "exx_dev.h"
 #include "kernels.h"
 
@@ -1257,6 +1259,728 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
     }
 }
 
+// ===========================================================================
+// Cluster path: one pair per cluster of kClusterCTAs CTAs.  The pair's FP32 CG
+// state lives in the cluster's distributed shared memory: CTA c holds r, q, e
+// of its contiguous range of aligned groups and p of the box rows that hold
+// them (row partition of the set, built on the host); the stencil reads p of
+// rows owned by other CTAs through shared::cluster loads.  Everything a pair
+// needs outside the CG (density, moments, far field, FP64 residuals, x, E,
+// sigma, D) is split over the CTAs by index range; CTA partial sums meet in
+// shared memory and every CTA adds them in rank order, so all CTAs take the
+// same decisions.
+// ===========================================================================
+struct ClusterWork {
+    char *base;                 // per-cluster slots (v box, rho, FP64 residual)
+    size_t slot_bytes;
+    size_t off_vbox, off_rho, off_r64;
+    int rowtab_words;           // row-table entries (largest B0 * B1 of the launch)
+    int p_floats;               // floats of the p region (largest over sets and CTAs, multiple of 4)
+    int max_groups;             // groups of r, q, e per CTA
+};
+
+__device__ __forceinline__ unsigned cl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cl_nrank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cl_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+// Cluster-wide barrier: release of this thread's prior writes, acquire of the others'.
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cl_map(unsigned a, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float4 cl_ld4(unsigned a)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float cl_ld(unsigned a)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double cl_ldd(unsigned a)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int cl_ldi(unsigned a)
+{
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void cl_st4(unsigned a, float x, float y, float z, float w)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+__device__ __forceinline__ void cl_st(unsigned a, float x)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
+}
+
+// Shared state of the cluster solver's reductions.
+struct ClusterRed {
+    double *red;                // CTA reduction scratch (block_sum)
+    double (*part)[64];         // [2][64] this CTA's partial sums, double-buffered by reduction count
+    double *out;                // [64] cluster totals, broadcast to the CTA
+    int par;
+    unsigned nrank;
+};
+
+// Sum K doubles over the cluster; every thread of every CTA receives the totals,
+// added in rank order (identical in all CTAs).
+template <int K>
+__device__ __forceinline__ void cl_sum(double (&v)[K], ClusterRed &R)
+{
+    block_sum<K>(v, R.red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) R.part[R.par][k] = v[k];
+    cl_sync();
+    if (threadIdx.x < K) {
+        const unsigned a = smem_u32(&R.part[R.par][threadIdx.x]);
+        double acc = 0.0;
+        for (unsigned c = 0; c < R.nrank; ++c) acc += cl_ldd(cl_map(a, c));
+        R.out[threadIdx.x] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = R.out[k];
+    R.par ^= 1;
+}
+
+// Sum K double-float values over the cluster in FP32 arithmetic; the totals
+// (as doubles) end up in R.out[0..K) after the call, in every CTA alike.
+template <int K>
+__device__ __forceinline__ void cl_sum_df(DF (&v)[K], ClusterRed &R)
+{
+    float2 *red2 = reinterpret_cast<float2 *>(R.red);
+    block_sum_df<K>(v, red2);
+    float2 *mine = reinterpret_cast<float2 *>(R.part[R.par]);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) mine[k] = make_float2(v[k].hi, v[k].lo);
+    cl_sync();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned a = smem_u32(mine);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            DF t = {0.f, 0.f};
+            if (lane < (int)R.nrank) {
+                const unsigned ak = cl_map(a + 8u * k, lane);
+                t.hi = cl_ld(ak);
+                t.lo = cl_ld(ak + 4u);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const DF u = {__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+                t = df_sum(t, u);
+            }
+            if (lane == 0) R.out[k] = (double)t.hi + (double)t.lo;
+        }
+    }
+    __syncthreads();
+    R.par ^= 1;
+}
+
+// FP64 residual b - A v (Eq. pe) on PE points k0 .. k1; returns this thread's sum of squares.
+__device__ __forceinline__ double residual_range(const SetDev &S, const double *__restrict__ vbox,
+                                                 const double *__restrict__ rho, double *__restrict__ r64,
+                                                 const double (*cw)[8], const int *ds, int ndir, int n, double center,
+                                                 int k0, int k1)
+{
+    double acc = 0.0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        const double r = kFourPi * rho[k] + lap_at<double>(vbox, off, cw, ds, ndir, n, center);
+        r64[k] = r;
+        acc += r * r;
+    }
+    return acc;
+}
+
+// Stencil of one own group with p read from the cluster's row storage.
+template <int FDN>
+__device__ __forceinline__ float4 cl_stencil(const unsigned *__restrict__ rowtab, int rid, int col, int mask,
+                                             const float (*cw)[8], float center, const int *drow, const int *dcol,
+                                             int ndir, float4 &cout)
+{
+    const unsigned rb = rowtab[rid] + 4u * (unsigned)col;
+    const float4 c = cl_ld4(rb);
+    const float4 cm = cl_ld4(rb - 16u);
+    const float4 cp = cl_ld4(rb + 16u);
+    const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
+    float acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
+#pragma unroll
+    for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (d == 2 || d >= ndir) continue;
+        const int dr = drow[d], dc = dcol[d];
+        if (dc == 0) {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_) {
+                const float4 a = cl_ld4(rowtab[rid + s_ * dr] + 4u * (unsigned)col);
+                const float4 b = cl_ld4(rowtab[rid - s_ * dr] + 4u * (unsigned)col);
+                acc[0] += cw[d][s_] * (a.x + b.x);
+                acc[1] += cw[d][s_] * (a.y + b.y);
+                acc[2] += cw[d][s_] * (a.z + b.z);
+                acc[3] += cw[d][s_] * (a.w + b.w);
+            }
+        } else {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_) {
+                const unsigned pa = rowtab[rid + s_ * dr] + (unsigned)(4 * (col + s_ * dc));
+                const unsigned pb = rowtab[rid - s_ * dr] + (unsigned)(4 * (col - s_ * dc));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (cl_ld(pa + 4u * i) + cl_ld(pb + 4u * i));
+            }
+        }
+    }
+    cout = c;
+    return make_float4((mask & 1) ? -acc[0] : 0.f, (mask & 2) ? -acc[1] : 0.f, (mask & 4) ? -acc[2] : 0.f,
+                       (mask & 8) ? -acc[3] : 0.f);
+}
+
+struct ClusterCg {
+    const SetDev *S;
+    const SmemCell *sm;
+    double *vbox;
+    const double *rho;
+    double *r64;
+    const unsigned *rowtab;
+    float4 *r4, *q4, *e4;
+    int G0, G1, K0, K1;
+    int ndir, fdn, max_iter;
+    double stop, bn, r0n, inner_red;
+    const int *drow, *dcol;
+};
+
+// Mixed-precision CG of one pair on the cluster: the arithmetic of
+// cg_mixed_sweep (FP32 in a frame scaled by the last true residual norm,
+// line-search alpha, Hestenes-Stiefel beta, FP64 replacements with a
+// conjugate restart), with the update of iteration k done before the stencil
+// of iteration k+1 and one cluster barrier between them.
+template <int FDN>
+__device__ __forceinline__ void cg_cluster(const ClusterCg &g, ClusterRed &R, int &iters, int &refine, int &status,
+                                           double &rnorm)
+{
+    const SetDev &S = *g.S;
+    const SmemCell &sm = *g.sm;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ngo = g.G1 - g.G0;
+    const int32_t *__restrict__ grp = S.groups;
+    const int32_t *__restrict__ grc = S.cl_grc;
+    const int32_t *__restrict__ pegl = S.cl_pe_gl;
+    const unsigned *__restrict__ rowtab = g.rowtab;
+    float4 *__restrict__ r4 = g.r4;
+    float4 *__restrict__ q4 = g.q4;
+    float4 *__restrict__ e4 = g.e4;
+    const float(*cw)[8] = sm.cw32;
+    const float center = sm.center32;
+    if (!(g.bn > 0.0) || !(g.r0n > g.stop)) return;
+    __shared__ struct {
+        double rr, rmax, S, pq;
+        float alpha, beta;
+        int act;
+    } cs;
+    // first frame: r = p = (b - A v0) / |b - A v0| on own PE points
+    {
+        DF a[1] = {{0.f, 0.f}};
+        const double sc = 1.0 / g.r0n;
+        for (int k = g.K0 + tid; k < g.K1; k += nt) {
+            const int gl = pegl[k];
+            const int gi = gl >> 2, lane = gl & 3;
+            const int w = grc[gi];
+            const float r = (float)(g.r64[k] * sc);
+            reinterpret_cast<float *>(&r4[gi - g.G0])[lane] = r;
+            cl_st(rowtab[w & 8191] + 4u * (unsigned)((w >> 13) + lane), r);
+            df_fma(a[0], r, r);
+        }
+        cl_sum_df<1>(a, R);
+        if (tid == 0) {
+            cs.rr = R.out[0];
+            cs.rmax = sqrt(R.out[0]);
+            cs.S = g.r0n;
+        }
+        __syncthreads();
+    }
+    bool pending = false;
+    float alpha_p = 0.f, beta_p = 0.f;
+    for (;;) {
+        if (iters >= g.max_iter) {
+            status = 5;
+            break;
+        }
+        DF dv[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // <p,q> <q,q> <r,q> <r,p> <r,r>
+        if (pending) {
+            for (int lg = tid; lg < ngo; lg += nt) {
+                const int w = grc[g.G0 + lg];
+                const unsigned pa = rowtab[w & 8191] + 4u * (unsigned)(w >> 13);
+                const float4 r = r4[lg], q = q4[lg], e = e4[lg], p_ = cl_ld4(pa);
+                const float r0 = r.x - alpha_p * q.x, r1 = r.y - alpha_p * q.y, r2 = r.z - alpha_p * q.z,
+                            r3 = r.w - alpha_p * q.w;
+                df_add(dv[4], r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+                r4[lg] = make_float4(r0, r1, r2, r3);
+                e4[lg] = make_float4(e.x + alpha_p * p_.x, e.y + alpha_p * p_.y, e.z + alpha_p * p_.z,
+                                     e.w + alpha_p * p_.w);
+                cl_st4(pa, r0 + beta_p * p_.x, r1 + beta_p * p_.y, r2 + beta_p * p_.z, r3 + beta_p * p_.w);
+            }
+        }
+        cl_sync();   // every CTA's p rows are current
+        for (int lg = tid; lg < ngo; lg += nt) {
+            const int gi = g.G0 + lg;
+            const int w = grc[gi];
+            float4 c;
+            const float4 q = cl_stencil<FDN>(rowtab, w & 8191, w >> 13, __ldg(grp + gi) & 15, cw, center, g.drow,
+                                             g.dcol, g.ndir, c);
+            q4[lg] = q;
+            const float4 r = r4[lg];
+            df_add(dv[0], c.x * q.x + c.y * q.y + c.z * q.z + c.w * q.w);
+            df_add(dv[1], q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+            df_add(dv[2], r.x * q.x + r.y * q.y + r.z * q.z + r.w * q.w);
+            df_add(dv[3], r.x * c.x + r.y * c.y + r.z * c.z + r.w * c.w);
+        }
+        cl_sum_df<5>(dv, R);
+        if (tid == 0) {
+            const double *d = R.out;
+            const double rr_ = pending ? d[4] : cs.rr;
+            const double alpha_d = d[3] / d[0];
+            const double rn = rr_ - 2.0 * alpha_d * d[2] + alpha_d * alpha_d * d[1];
+            const double rnrm = sqrt(fmax(rn, 0.0));
+            const bool breakdown = !(d[0] > 0.0) || !(d[3] > 0.0) || !(alpha_d < 1e300);
+            int act = 0;
+            if (breakdown) act = 2;
+            else if (!(rn > 0.0) || rnrm <= g.inner_red * cs.rmax || rnrm * cs.S <= 0.5 * g.stop) act = 1;
+            cs.alpha = breakdown ? 0.f : (float)alpha_d;
+            cs.beta = breakdown ? 0.f : (float)(-(d[2] - alpha_d * d[1]) / d[0]);
+            cs.pq = d[0];
+            cs.rr = rn;
+            cs.act = act;
+        }
+        __syncthreads();
+        const int act = cs.act;
+        const float alpha = cs.alpha;
+        pending = false;
+        ++iters;
+        if (act) {
+            // x += S (e + alpha p) in FP64 on own PE points
+            const double S_ = cs.S;
+            for (int k = g.K0 + tid; k < g.K1; k += nt) {
+                const int gl = pegl[k];
+                const int gi = gl >> 2, lane = gl & 3;
+                const int w = grc[gi];
+                float *ep = reinterpret_cast<float *>(&e4[gi - g.G0]) + lane;
+                const float pv = cl_ld(rowtab[w & 8191] + 4u * (unsigned)((w >> 13) + lane));
+                g.vbox[S.pe_off[k]] += ((double)*ep + (double)alpha * (double)pv) * S_;
+                *ep = 0.f;
+            }
+            __threadfence();
+            cl_sync();
+            double rr2[1] = {residual_range(S, g.vbox, g.rho, g.r64, sm.cw64, sm.ds, g.ndir, g.fdn, sm.center64,
+                                            g.K0, g.K1)};
+            cl_sum<1>(rr2, R);
+            rnorm = sqrt(rr2[0]);
+            ++refine;
+            if (rnorm <= g.stop) break;
+            const double sc = 1.0 / rnorm;
+            DF ab[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            for (int k = g.K0 + tid; k < g.K1; k += nt) {
+                const int gl = pegl[k];
+                const int lg = (gl >> 2) - g.G0, lane = gl & 3;
+                const float r = (float)(g.r64[k] * sc);
+                reinterpret_cast<float *>(&r4[lg])[lane] = r;
+                df_fma(ab[0], r, r);
+                df_fma(ab[1], r, reinterpret_cast<const float *>(&q4[lg])[lane]);
+            }
+            cl_sum_df<2>(ab, R);
+            if (tid == 0) {
+                cs.beta = act == 2 ? 0.f : (float)(-R.out[1] / cs.pq);   // gamma of the carried direction
+                cs.rr = R.out[0];
+                cs.rmax = sqrt(R.out[0]);
+                cs.S = rnorm;
+            }
+            __syncthreads();
+            const float gamma = cs.beta;
+            for (int lg = tid; lg < ngo; lg += nt) {
+                const int w = grc[g.G0 + lg];
+                const unsigned pa = rowtab[w & 8191] + 4u * (unsigned)(w >> 13);
+                const float4 r = r4[lg], p_ = cl_ld4(pa);
+                cl_st4(pa, r.x + gamma * p_.x, r.y + gamma * p_.y, r.z + gamma * p_.z, r.w + gamma * p_.w);
+            }
+            continue;
+        }
+        alpha_p = alpha;
+        beta_p = cs.beta;
+        pending = true;
+    }
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_pair_solve_cluster(const CellDev *__restrict__ cells, ListDev L,
+                                                                         ClusterWork W, int inner_shift)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ SmemCell sm;
+    __shared__ double red[33 * 10 + 64];
+    __shared__ double s_part[2][64];
+    __shared__ double s_out[64];
+    __shared__ int s_pair, s_t, s_cell, s_set, s_flag;
+    __shared__ int s_drow[6], s_dcol[6];
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const unsigned rank = cl_rank(), nrank = cl_nrank();
+    char *slot = W.base + (size_t)cl_id() * W.slot_bytes;
+    double *vbox = (double *)(slot + W.off_vbox);
+    double *rho = (double *)(slot + W.off_rho);
+    double *r64 = (double *)(slot + W.off_r64);
+    unsigned *rowtab = reinterpret_cast<unsigned *>(dyn);
+    float *preg = reinterpret_cast<float *>(dyn + (((size_t)4 * W.rowtab_words + 15) & ~(size_t)15));
+    float4 *r4 = reinterpret_cast<float4 *>(preg + W.p_floats);
+    float4 *q4 = r4 + W.max_groups;
+    float4 *e4 = q4 + W.max_groups;
+    const unsigned p_s = smem_u32(preg);
+    const double inner_red = ldexp(1.0, -inner_shift);
+    ClusterRed R;
+    R.red = red;
+    R.part = s_part;
+    R.out = s_out;
+    R.par = 0;
+    R.nrank = nrank;
+
+    if (tid == 0) {
+        s_cell = -1;
+        s_set = -1;
+    }
+    for (;;) {
+        if (rank == 0 && tid == 0) s_pair = atomicAdd(L.queue, 1);
+        cl_sync();
+        if (tid == 0) s_t = cl_ldi(cl_map(smem_u32(&s_pair), 0));
+        __syncthreads();
+        const int t = s_t;
+        if (t >= *L.total) break;
+        const PairRec pr = L.pairs[t];
+        const int self = (pr.i == pr.j);
+        if (pr.cell != s_cell) {
+            const int *src = (const int *)&cells[pr.cell];
+            int *dst = (int *)&sm.C;
+            for (int k = tid; k < (int)(sizeof(CellDev) / sizeof(int)); k += nt) dst[k] = src[k];
+            __syncthreads();
+            if (tid < 48) {
+                const int d = tid / 8, s = tid % 8;
+                sm.cw64[d][s] = sm.C.cw64[d][s];
+                sm.cw32[d][s] = sm.C.cw32[d][s];
+            }
+            if (tid == 0) {
+                double c = 0.0;
+                for (int d = 0; d < sm.C.ndir; ++d) c += sm.C.cw64[d][0];
+                sm.center64 = c;
+                sm.center32 = (float)c;
+                s_cell = pr.cell;
+                s_set = -1;
+            }
+            __syncthreads();
+        }
+        const CellDev &C = sm.C;
+        const SetDev &S = C.set[self ? 0 : 1];
+        const int ndir = C.ndir, fdn = C.fd_n;
+        if (s_set != self) {
+            // row table of this set: shared::cluster address of column 0 of every box row
+            const int nrows = S.B[0] * S.B[1];
+            for (int rid = tid; rid < nrows; rid += nt) {
+                const int own = S.cl_rows[2 * rid];
+                unsigned a = 0;
+                if (own >= 0) a = cl_map(p_s + 4u * (unsigned)S.cl_rows[2 * rid + 1], (unsigned)own);
+                else if (own == -2) a = cl_map(p_s + 4u * (unsigned)S.cl_pad, rank);
+                rowtab[rid] = a;
+            }
+            if (tid < 6) {
+                s_drow[tid] = tid < ndir ? C.dir[tid][0] * S.B[1] + C.dir[tid][1] : 0;
+                s_dcol[tid] = tid < ndir ? C.dir[tid][2] : 0;
+                sm.ds[tid] = S.dstride[tid];
+            }
+            __syncthreads();
+            if (tid == 0) s_set = self;
+        }
+        if (tid == 0) s_flag = 0;
+        const int32_t *cta = S.cl_cta + 8 * rank;
+        const int G0 = cta[0], G1 = cta[1], K0 = cta[2], K1 = cta[3];
+        __syncthreads();
+
+        // ---- Step III: pair density on own PE points (Eq. l2g) ----
+        for (int k = K0 + tid; k < K1; k += nt) {
+            int m0, m1, m2;
+            unpack_m(S.pe_m[k], m0, m1, m2);
+            const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
+                      g2 = wrapi(pr.g[2] + m2, C.n[2]);
+            rho[k] = phi_at(C, pr.i, g0, g1, g2) * phi_at(C, pr.j, g0, g1, g2);
+        }
+        __syncthreads();
+
+        // ---- moments Q_lm (Eq. mepole): own PE points, then the cluster sum ----
+        {
+            double *wpart = reinterpret_cast<double *>(q4);   // [nwarps][kNlm] scratch (CG state not live yet)
+            double a0 = 0.0, a1 = 0.0;
+            const int nchunk = (K1 - K0 + 31) >> 5;
+            for (int ch = warp; ch < nchunk; ch += nwarps) {
+                const int k0 = K0 + (ch << 5);
+                const float rlf = (k0 + lane < K1) ? (float)rho[k0 + lane] : 0.f;
+                const int cnt = min(32, K1 - k0);
+                float f0 = 0.f, f1 = 0.f;
+                for (int p = 0; p < cnt; ++p) {
+                    const float rp = __shfl_sync(0xffffffffu, rlf, p);
+                    const float *row = S.S32 + (size_t)(k0 + p) * kNlm;
+                    f0 += rp * row[lane];
+                    if (lane + 32 < kNlm) f1 += rp * row[lane + 32];
+                }
+                a0 += f0;
+                a1 += f1;
+            }
+            wpart[warp * kNlm + lane] = a0;
+            if (lane + 32 < kNlm) wpart[warp * kNlm + lane + 32] = a1;
+            __syncthreads();
+            if (tid < kNlm) {
+                double s = 0.0;
+                for (int w = 0; w < nwarps; ++w) s += wpart[w * kNlm + tid];
+                s_part[R.par][tid] = s;
+            }
+            cl_sync();
+            if (tid < kNlm) {
+                const unsigned a = smem_u32(&s_part[R.par][tid]);
+                double s = 0.0;
+                for (unsigned c = 0; c < nrank; ++c) s += cl_ldd(cl_map(a, c));
+                const double q = (tid < (C.lmax + 1) * (C.lmax + 1)) ? s * C.dv : 0.0;
+                sm.Q[tid] = q;
+                sm.Qf[tid] = (float)q;
+            }
+            R.par ^= 1;
+            __syncthreads();
+        }
+
+        // ---- far field on this CTA's share of the halo (Eq. me) ----
+        {
+            const int h0 = (int)(((long long)S.n_halo * rank) / nrank);
+            const int h1 = (int)(((long long)S.n_halo * (rank + 1)) / nrank);
+            for (int h = h0 + tid; h < h1; h += nt) {
+                float vf = 0.f;
+                for (int lm = 0; lm < kNlm; ++lm) vf += sm.Qf[lm] * S.T32[(size_t)lm * S.n_shell + h];
+                vbox[S.halo_off[h]] = vf;
+            }
+        }
+        // CG state of this CTA: all zero (p rows including the zero row; r, q, e)
+        for (int i = tid; i < (W.p_floats >> 2); i += nt)
+            reinterpret_cast<float4 *>(preg)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < G1 - G0; i += nt) {
+            r4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            q4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            e4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __threadfence();
+        cl_sync();
+
+        // ---- Step IV: Poisson solve (Eq. pe) ----
+        double bb[1] = {residual_range(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, K0, K1)};
+        cl_sum<1>(bb, R);
+        const double bn = sqrt(bb[0]);
+        const double stop = C.tol * bn;
+        int iters = 0, refine = 1, status = 0;
+        double rnorm = bn;
+        int warm = -1;
+        int dg[3] = {0, 0, 0};
+        if (C.warm_map && bn > 0.0) {
+            const int o = C.warm_map[(size_t)pr.i * C.n_orb + pr.j];
+            if (o >= 0) {
+                const PairRec q = C.warm_rows[o];
+                if (q.i == pr.i && q.j == pr.j && q.k[0] == pr.k[0] && q.k[1] == pr.k[1] && q.k[2] == pr.k[2]) {
+                    warm = o;
+                    for (int a = 0; a < 3; ++a) {
+                        int d = wrapi(pr.g[a] - q.g[a], C.n[a]);
+                        if (2 * d >= C.n[a]) d -= C.n[a];
+                        dg[a] = d;
+                    }
+                }
+            }
+        }
+        if (warm >= 0) {
+            const int32_t *inv = C.warm_inv[self ? 0 : 1];
+            const float *src = C.warm_prev + (size_t)warm * C.warm_stride;
+            for (int k = K0 + tid; k < K1; k += nt) {
+                int m0, m1, m2;
+                unpack_m(S.pe_m[k], m0, m1, m2);
+                const int u0 = m0 + dg[0] + S.c[0], u1 = m1 + dg[1] + S.c[1], u2 = m2 + dg[2] + S.c[2];
+                double v = 0.0;
+                if (u0 >= 0 && u0 < S.B[0] && u1 >= 0 && u1 < S.B[1] && u2 >= 0 && u2 < S.B[2]) {
+                    const int kk = inv[((size_t)u0 * S.B[1] + u1) * S.B[2] + u2];
+                    if (kk >= 0) v = (double)src[kk];
+                }
+                vbox[S.pe_off[k]] = v;
+            }
+            __threadfence();
+            cl_sync();
+            double r0[1] = {residual_range(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, K0, K1)};
+            cl_sum<1>(r0, R);
+            rnorm = sqrt(r0[0]);
+            ++refine;
+        }
+        {
+            ClusterCg g;
+            g.S = &S;
+            g.sm = &sm;
+            g.vbox = vbox;
+            g.rho = rho;
+            g.r64 = r64;
+            g.rowtab = rowtab;
+            g.r4 = r4;
+            g.q4 = q4;
+            g.e4 = e4;
+            g.G0 = G0;
+            g.G1 = G1;
+            g.K0 = K0;
+            g.K1 = K1;
+            g.ndir = ndir;
+            g.fdn = fdn;
+            g.max_iter = C.max_iter;
+            g.stop = stop;
+            g.bn = bn;
+            g.r0n = rnorm;
+            g.inner_red = inner_red;
+            g.drow = s_drow;
+            g.dcol = s_dcol;
+            switch (fdn) {
+            case 1: cg_cluster<1>(g, R, iters, refine, status, rnorm); break;
+            case 2: cg_cluster<2>(g, R, iters, refine, status, rnorm); break;
+            case 3: cg_cluster<3>(g, R, iters, refine, status, rnorm); break;
+            default: cg_cluster<4>(g, R, iters, refine, status, rnorm); break;
+            }
+        }
+        // the final x of every CTA is visible to all CTAs of the cluster
+        __threadfence();
+        cl_sync();
+
+        if (C.warm_next) {
+            const int tl = t - L.cell_start[pr.cell];
+            if (tl >= 0 && tl < C.warm_cap) {
+                float *dst = C.warm_next + (size_t)tl * C.warm_stride;
+                for (int k = K0 + tid; k < K1; k += nt) dst[k] = (float)vbox[S.pe_off[k]];
+            }
+        }
+
+        // ---- D^i += v phi_j, D^j += v phi_i on this CTA's share of PE and shell (Eq. Dxx) ----
+        if (C.dxx) {
+            bool ok = true;
+            const int nme = S.n_pe + S.n_shell;
+            const int q0 = (int)(((long long)nme * rank) / nrank), q1 = (int)(((long long)nme * (rank + 1)) / nrank);
+            for (int k = q0 + tid; k < q1; k += nt) {
+                int m0, m1, m2;
+                double v;
+                if (k < S.n_pe) {
+                    unpack_m(S.pe_m[k], m0, m1, m2);
+                    v = vbox[S.pe_off[k]];
+                } else {
+                    const int s = k - S.n_pe;
+                    unpack_m(S.sh_m[s], m0, m1, m2);
+                    float vf = 0.f;
+                    for (int lm = 0; lm < kNlm; ++lm) vf += sm.Qf[lm] * S.T32[(size_t)lm * S.n_shell + s];
+                    v = vf;
+                }
+                const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
+                          g2 = wrapi(pr.g[2] + m2, C.n[2]);
+                const double fj = phi_at(C, pr.j, g0, g1, g2);
+                ok &= d_add(C, pr.i, g0, g1, g2, v * fj);
+                if (!self) {
+                    const double fi = phi_at(C, pr.i, g0, g1, g2);
+                    ok &= d_add(C, pr.j, g0, g1, g2, v * fi);
+                }
+            }
+            if (!ok) s_flag = 1;
+        }
+
+        // ---- Step V: energy and stress integrals on own PE points, cluster sums ----
+        double acc[11];
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc[k] = 0.0;
+        const bool want_sigma = C.stress_mode != 2;
+        for (int k = K0 + tid; k < K1; k += nt) {
+            const int off = S.pe_off[k];
+            const double rk = rho[k];
+            acc[0] += rk * vbox[off];
+            if (!want_sigma) continue;
+            double dxi[3];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                const int st = S.gstride[al];
+                double tt = 0.0;
+#pragma unroll
+                for (int s = 1; s <= 6; ++s)
+                    if (s <= fdn) tt += C.w1dx[al][s] * (vbox[off + s * st] - vbox[off - s * st]);
+                dxi[al] = tt;
+            }
+            int m0, m1, m2;
+            unpack_m(S.pe_m[k], m0, m1, m2);
+            const double sb[3] = {(double)m0 / C.n[0], (double)m1 / C.n[1], (double)m2 / C.n[2]};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double dva = C.J[a][0] * dxi[0] + C.J[a][1] * dxi[1] + C.J[a][2] * dxi[2];
+                const double rdv = rk * dva;
+#pragma unroll
+                for (int al = 0; al < 3; ++al) acc[1 + 3 * a + al] += sb[al] * rdv;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) acc[10] = s_flag ? 1.0 : 0.0;
+        cl_sum<11>(acc, R);
+        if (rank == 0 && tid == 0) {
+            PairOut o;
+            o.e = acc[0] * C.dv;
+            for (int k = 0; k < 9; ++k) o.sig[k] = acc[1 + k] * C.dv;
+            o.iters = iters;
+            o.refine = refine;
+            o.status = status ? status : (acc[10] > 0.0 ? 7 : 0);
+            o.pad = warm >= 0 ? 1 : 0;
+            L.out[t] = o;
+        }
+        // every CTA has read v (epilogue, D); restore the all-zero v box
+        cl_sync();
+        for (int k = K0 + tid; k < K1; k += nt) vbox[S.pe_off[k]] = 0.0;
+        {
+            const int h0 = (int)(((long long)S.n_halo * rank) / nrank);
+            const int h1 = (int)(((long long)S.n_halo * (rank + 1)) / nrank);
+            for (int h = h0 + tid; h < h1; h += nt) vbox[S.halo_off[h]] = 0.0;
+        }
+        __threadfence();
+    }
+    cl_sync();   // no CTA leaves while another may still read its shared memory
+}
+
 // Ordered per-cell reductions (Eqs. exxGen_mlwf, sxx_working, pixx_working).
 __global__ void __launch_bounds__(256) k_finalize(const CellDev *__restrict__ cells, ListDev L, CellResult *res)
 {
@@ -1396,6 +2120,55 @@ cudaError_t launch_finalize(const CellDev *cells, int n_cells, const ListDev &L,
 }  // namespace exx
 
 namespace exx {
+cudaError_t launch_solve_cluster(const CellDev *cells, const ListDev &L, const SolveSlots &slots, int rowtab_words,
+                                 int p_floats, int max_groups, int inner_shift, int *n_clusters, cudaStream_t s)
+{
+    ClusterWork W;
+    W.base = slots.base;
+    W.slot_bytes = slots.slot_bytes;
+    W.off_vbox = slots.off_vbox;
+    W.off_rho = slots.off_rho;
+    W.off_r64 = slots.off_r64;
+    W.rowtab_words = rowtab_words;
+    W.p_floats = (p_floats + 3) & ~3;
+    W.max_groups = max_groups;
+    const size_t dyn = cluster_dyn_bytes(rowtab_words, p_floats, max_groups);
+    cudaError_t e = cudaFuncSetAttribute(k_pair_solve_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pair_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kClusterCTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kClusterCTAs, 1, 1);
+    int nc = 0;
+    e = cudaOccupancyMaxActiveClusters(&nc, k_pair_solve_cluster, &cfg);
+    if (e != cudaSuccess) return e;
+    nc = std::min(nc, slots.n_slots);
+    if (nc < 1) return cudaErrorInvalidConfiguration;
+    cfg.gridDim = dim3(kClusterCTAs * nc, 1, 1);
+    *n_clusters = nc;
+    return cudaLaunchKernelEx(&cfg, k_pair_solve_cluster, cells, L, W, inner_shift);
+}
+
+int cluster_capacity_bytes()
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_pair_solve_cluster) != cudaSuccess) return 0;
+    return std::max(0, optin - (int)fa.sharedSizeBytes - 1024);
+}
+
 int solve_blocks_per_sm(bool mixed)
 {
     int n = 0;

@@ -31,6 +31,24 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
                          int inner_shift, cudaStream_t s);
 cudaError_t launch_finalize(const CellDev *cells, int n_cells, const ListDev &L, CellResult *res, cudaStream_t s);
 int solve_blocks_per_sm(bool mixed);
+
+// Cluster path of the mixed solver: one pair per cluster of kClusterCTAs CTAs
+// with the CG state in distributed shared memory.
+constexpr int kClusterCTAs = 16;
+#ifndef EXX_CLUSTER_THREADS
+#define EXX_CLUSTER_THREADS 512
+#endif
+constexpr int kClusterThreads = EXX_CLUSTER_THREADS;   // threads per cluster CTA
+inline size_t cluster_dyn_bytes(int rowtab_words, int p_floats, int max_groups)
+{
+    return ((4 * (size_t)rowtab_words + 15) & ~(size_t)15) + 4 * (size_t)((p_floats + 3) & ~3) +
+           48 * (size_t)max_groups;
+}
+// Largest dynamic shared memory a cluster CTA can take on the current device.
+int cluster_capacity_bytes();
+// Launches as many clusters as can be resident (at most slots.n_slots); *n_clusters receives the count.
+cudaError_t launch_solve_cluster(const CellDev *cells, const ListDev &L, const SolveSlots &slots, int rowtab_words,
+                                 int p_floats, int max_groups, int inner_shift, int *n_clusters, cudaStream_t s);
 cudaError_t launch_warm_map(const PairRec *rows, int n, int n_orb, int *map, cudaStream_t s);
 
 }  // namespace exx

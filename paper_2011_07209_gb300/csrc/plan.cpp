@@ -462,4 +462,81 @@ int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L)
     return EXX_OK;
 }
 
+int make_cluster_part(const SetLayout &L, const Stencil &st, int fd_n, int nc, ClusterPart &cp)
+{
+    cp = ClusterPart();
+    cp.nc = nc;
+    const int ng = (int)L.groups.size();
+    if (nc < 1 || ng == 0) return EXX_ERR_ARG;
+    const int B0 = L.B[0], B1 = L.B[1], B2 = L.B[2];
+    if ((long long)B0 * B1 >= (1 << 13) || B2 >= (1 << 18)) return EXX_ERR_ARG;
+    int reach2 = 0;
+    for (int d = 0; d < st.ndir; ++d) reach2 = std::max(reach2, fd_n * std::abs(st.dir[d][2]));
+    // the 12-wide window reads columns x - 4 .. x + 7 of a group at x
+    cp.pad = (std::max(4, reach2) + 3) & ~3;
+    cp.row_stride = (cp.pad + B2 + std::max(8, reach2 + 4) + 3) & ~3;
+    // rows that hold PE points (stored), rows that hold only halo points (read as
+    // zeros: mapped to a zero row), and PE groups per row
+    const long long nrow = (long long)B0 * B1;
+    std::vector<char> used(nrow, 0);
+    std::vector<int> gcount(nrow, 0);
+    for (int32_t off : L.halo_off) used[off / B2] = 2;
+    for (int32_t off : L.pe_off) used[off / B2] = 1;
+    cp.grc.resize(ng);
+    for (int g = 0; g < ng; ++g) {
+        const long long off = (long long)(L.groups[g] >> 4) << 2;
+        const long long rid = off / B2;
+        gcount[rid]++;
+        cp.grc[g] = (int32_t)(rid | ((off % B2) << 13));
+    }
+    // contiguous row ranges with about ng / nc groups each
+    cp.cta.assign((size_t)nc * 8, 0);
+    cp.rows.assign((size_t)nrow * 2, 0);
+    for (long long r = 0; r < nrow; ++r) cp.rows[2 * r] = -1;
+    std::vector<long long> first_row(nc + 1, nrow);
+    {
+        long long cum = 0;
+        int c = 0;
+        first_row[0] = 0;
+        for (long long r = 0; r < nrow; ++r) {
+            while (c + 1 < nc && cum >= (long long)ng * (c + 1) / nc) first_row[++c] = r;
+            cum += gcount[r];
+        }
+        for (int k = c + 1; k <= nc; ++k) first_row[k] = nrow;
+    }
+    int g = 0, k = 0;
+    for (int c = 0; c < nc; ++c) {
+        int32_t *t = &cp.cta[8 * (size_t)c];
+        t[0] = g;
+        t[2] = k;
+        long long nstored = 1;   // row 0 of every CTA's region is the zero row
+        for (long long r = first_row[c]; r < first_row[c + 1]; ++r) {
+            g += gcount[r];
+            if (used[r] == 2) cp.rows[2 * r] = -2;
+            if (used[r] != 1) continue;
+            cp.rows[2 * r] = c;
+            cp.rows[2 * r + 1] = (int32_t)(nstored * cp.row_stride + cp.pad);
+            ++nstored;
+        }
+        while (k < L.n_pe && (long long)L.pe_off[k] / B2 < first_row[c + 1]) ++k;
+        t[1] = g;
+        t[3] = k;
+        t[4] = (int32_t)nstored;
+        if (nstored * cp.row_stride > (1LL << 30)) return EXX_ERR_ARG;
+        t[5] = (int32_t)(nstored * cp.row_stride);
+        cp.max_p_floats = std::max(cp.max_p_floats, t[5]);
+        cp.max_groups = std::max(cp.max_groups, t[1] - t[0]);
+    }
+    if (g != ng || k != L.n_pe) return EXX_ERR_ARG;
+    cp.pe_gl.resize(L.n_pe);
+    for (int q = 0, gg = 0; q < L.n_pe; ++q) {
+        const long long off = L.pe_off[q];
+        while (gg + 1 < ng && ((long long)(L.groups[gg + 1] >> 4) << 2) <= off) ++gg;
+        const long long go = (long long)(L.groups[gg] >> 4) << 2;
+        if (!(go <= off && off < go + 4)) return EXX_ERR_ARG;
+        cp.pe_gl[q] = (gg << 2) | (int)(off - go);
+    }
+    return EXX_OK;
+}
+
 }  // namespace exx

@@ -70,6 +70,27 @@ struct SetLayout {
 };
 int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
 
+// Row partition of one set over a cluster of nc CTAs (the cluster CG path).
+// The box rows (plane z, row y) that hold PE or halo points are taken in
+// (z, y) order and split into nc contiguous ranges with about equal numbers of
+// PE groups.  CTA c keeps p for its rows that hold PE points in shared memory,
+// each row as pad + B2 + pad2 floats (column x at pad + x), so that every
+// stencil read of a PE group -- including the lanes outside PE -- stays inside
+// one stored row; row 0 of every CTA's region is all zero and stands for the
+// rows that hold only halo points.
+struct ClusterPart {
+    int nc = 0;
+    int pad = 0, row_stride = 0;          // floats before column 0, floats per stored row
+    std::vector<int32_t> cta;             // [nc][8]: G0, G1, K0, K1, rows, p_floats, 0, 0
+    std::vector<int32_t> rows;            // [B0 * B1][2]: owner rank, float offset of column 0; owner -2:
+                                          // a row of halo points only (all zero: read the reader's zero
+                                          // row at offset pad); -1: never read
+    std::vector<int32_t> grc;             // [n_groups]: row id (z * B1 + y) | column << 13
+    std::vector<int32_t> pe_gl;           // [n_pe]: group index << 2 | lane of each PE point
+    int max_p_floats = 0, max_groups = 0;
+};
+int make_cluster_part(const SetLayout &L, const Stencil &st, int fd_n, int nc, ClusterPart &cp);
+
 // Packing of an offset triple with |m_alpha| <= 511 into one int32.
 inline int32_t pack_m(int m0, int m1, int m2) {
     return (int32_t)(((uint32_t)(m0 + 512) << 20) | ((uint32_t)(m1 + 512) << 10) | (uint32_t)(m2 + 512));

@@ -20,6 +20,7 @@ OK, ERR_ARG, ERR_CELL, ERR_HALO, ERR_NK, ERR_CG, ERR_CAPACITY, ERR_BOX, ERR_OOM,
 FP64, MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 STRESS_FULL, STRESS_ISOTROPIC, STRESS_CUBIC = 0, 1, 2
+SOLVER_CTA, SOLVER_CLUSTER = 0, 1
 
 _lib = None
 _lock = threading.Lock()
@@ -27,7 +28,7 @@ _lock = threading.Lock()
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
            "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version",
-           "exx_pair_list_noalloc")
+           "exx_pair_list_noalloc", "exx_ctx_set_solver")
 
 
 class Cell(C.Structure):
@@ -60,7 +61,7 @@ class PlanInfo(C.Structure):
                 ("n_halo_self", C.c_int), ("n_halo_pair", C.c_int), ("n_aux", C.c_int), ("n_stcl", C.c_int),
                 ("dirs", C.c_int * 18), ("coef", C.c_double * 6), ("aux_frozen", C.c_int * 9),
                 ("box_self", C.c_int * 3), ("box_pair", C.c_int * 3), ("workspace_bytes", C.c_longlong),
-                ("pair_capacity", C.c_int), ("ctas", C.c_int), ("threads", C.c_int)]
+                ("pair_capacity", C.c_int), ("ctas", C.c_int), ("threads", C.c_int), ("cluster", C.c_int)]
 
 
 class ExxError(RuntimeError):
@@ -105,6 +106,7 @@ def lib(build_if_missing: bool = False):
             L.exx_get_pair_list.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.exx_dbox_halfwidth.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(C.c_int)]
             L.exx_ctx_set_timing.argtypes = [C.c_void_p, C.c_int]
+            L.exx_ctx_set_solver.argtypes = [C.c_void_p, C.c_int]
             L.exx_pair_list_noalloc.argtypes = [C.POINTER(Cell), C.c_void_p, C.c_int, C.c_double, C.c_int,
                                                 C.c_void_p, C.c_void_p, C.c_void_p]
             L.exx_ctx_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
@@ -183,6 +185,10 @@ class Context:
     def set_timing(self, enable: bool = True):
         _check(lib().exx_ctx_set_timing(self.handle, int(enable)), "exx_ctx_set_timing")
 
+    def set_solver(self, solver: int):
+        """SOLVER_CTA (default) or SOLVER_CLUSTER for the mixed-precision pair solver."""
+        _check(lib().exx_ctx_set_solver(self.handle, int(solver)), "exx_ctx_set_solver")
+
     def timing(self) -> dict:
         ms = (C.c_double * 4)()
         _check(lib().exx_ctx_get_timing(self.handle, ms), "exx_ctx_get_timing")
@@ -222,7 +228,7 @@ class Plan:
             "n_aux": pi.n_aux, "n_stcl": pi.n_stcl,
             "dirs": np.array(list(pi.dirs)).reshape(6, 3)[:3 + pi.n_aux], "coef": np.array(list(pi.coef))[:3 + pi.n_aux],
             "box_self": list(pi.box_self), "box_pair": list(pi.box_pair), "workspace_bytes": pi.workspace_bytes,
-            "pair_capacity": pi.pair_capacity, "ctas": pi.ctas, "threads": pi.threads,
+            "pair_capacity": pi.pair_capacity, "ctas": pi.ctas, "threads": pi.threads, "cluster": pi.cluster,
         }
 
     def pair_list(self) -> np.ndarray:

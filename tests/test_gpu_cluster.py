@@ -1,0 +1,121 @@
+"""GPU: the cluster pair solver (EXX_SOLVER_CLUSTER), which keeps each pair's
+FP32 CG state in the distributed shared memory of a 16-CTA cluster.
+
+It must agree with the oracle on small cells (cubic, triclinic with the
+37-point stencil), with the one-CTA solver on the full 64-molecule cell and
+on a warm-started frozen trajectory, and fall back to the one-CTA solver
+for subdomains too large for the cluster's shared memory.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2011_07209_gb300.synth as synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_07209_gb300 import exx
+    cl = exx.Context(0)
+    cl.set_solver(exx.SOLVER_CLUSTER)
+    cta = exx.Context(0)
+    yield cl, cta
+    cl.close()
+    cta.close()
+
+
+def _run(ctx, ws, p, plan=None, want_d=True):
+    from paper_2011_07209_gb300 import driver
+    cr = driver.prepare(ctx, ws, p, plan=plan, want_d=want_d)
+    out = driver.run(ctx, cr)
+    out["dxx"] = cr.dxx.cpu().numpy() if want_d else None
+    out["dbox"], out["dbox_lo"] = cr.dbox, cr.dbox_lo_np
+    out["info"] = cr.plan.info()
+    return out
+
+
+def _check_oracle(g, o):
+    assert np.array_equal(g["pairs"], o["pairs"])
+    assert g["e_xx"] == pytest.approx(o["e_xx"], rel=1e-7)
+    assert np.abs(g["stress"] - o["stress"]).max() < 1e-8
+    assert (np.abs(g["pair_e"] - o["pair_e"]) / np.abs(o["pair_e"]).max()).max() < 1e-6
+    if o["dxx"] is not None:
+        assert np.abs(g["dxx"] - o["dxx"]).max() < 1e-6
+
+
+def test_cluster_solver_small_cubic_cell(ctxs):
+    from paper_2011_07209_gb300 import exx
+    cl, _ = ctxs
+    ws = synth.make_config(1)
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED)
+    g = _run(cl, ws, p)
+    assert g["info"]["cluster"] == 16 and g["status"] == 0
+    o = oracle.exx(ws, oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10), dbox=g["dbox"],
+                   dbox_lo=g["dbox_lo"])
+    _check_oracle(g, o)
+
+
+def test_cluster_solver_triclinic_37_point_stencil(ctxs):
+    from paper_2011_07209_gb300 import exx
+    cl, _ = ctxs
+    lat = 14.0 * np.array([[1.0, 0.0, 0.0], [0.1, 1.0, 0.0], [0.05, -0.08, 1.0]])
+    ws = synth.water_cell(lat, (56, 56, 56), 3, 5)
+    p = exx.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10, precision=exx.MIXED)
+    g = _run(cl, ws, p)
+    assert g["info"]["cluster"] == 16 and g["n_stcl"] == 37
+    o = oracle.exx(ws, oracle.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10), dbox=g["dbox"],
+                   dbox_lo=g["dbox_lo"])
+    _check_oracle(g, o)
+
+
+def test_cluster_matches_cta_solver_full_size(ctxs):
+    from paper_2011_07209_gb300 import exx
+    cl, cta = ctxs
+    ws = synth.make_config(2)
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, precision=exx.MIXED)
+    a = _run(cl, ws, p, want_d=True)
+    b = _run(cta, ws, p, want_d=True)
+    assert a["info"]["cluster"] == 16 and b["info"]["cluster"] == 1
+    assert a["status"] == 0 and b["status"] == 0
+    assert np.array_equal(a["pairs"], b["pairs"])
+    assert a["e_xx"] == pytest.approx(b["e_xx"], rel=1e-9)
+    assert (np.abs(a["pair_e"] - b["pair_e"]) / np.abs(b["pair_e"]).max()).max() < 1e-7
+    assert np.abs(a["stress"] - b["stress"]).max() < 1e-10
+    assert np.abs(a["dxx"] - b["dxx"]).max() < 1e-7
+    assert abs(a["pair_iter"].mean() - b["pair_iter"].mean()) < 1.0
+
+
+def test_cluster_warm_started_frozen_trajectory(ctxs):
+    from paper_2011_07209_gb300 import exx
+    cl, cta = ctxs
+    ws0 = synth.make_config(1)
+    steps = synth.trajectory(ws0, 2, seed=synth.SEED_BASE + 51, strain_sigma=1e-3, centre_sigma=0.02)
+    box = np.max([w.box for w in steps], axis=0)
+    steps = [w.padded(box) for w in steps]
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, frozen=True, warm_start=True)
+    plan_cl = exx.Plan(cl, ws0.lattice, ws0.n, p, ws0.n_orb, box)
+    plan_cta = exx.Plan(cta, ws0.lattice, ws0.n, p, ws0.n_orb, box)
+    for k, ws in enumerate(steps):
+        a = _run(cl, ws, p, plan=plan_cl, want_d=False)
+        b = _run(cta, ws, p, plan=plan_cta, want_d=False)
+        assert a["status"] == 0 and a["info"]["cluster"] == 16
+        assert a["n_warm"] == b["n_warm"] and (k == 0) == (a["n_warm"] == 0)
+        assert a["e_xx"] == pytest.approx(b["e_xx"], rel=1e-8)
+        assert np.abs(a["stress"] - b["stress"]).max() < 1e-10
+
+
+def test_cluster_falls_back_for_large_subdomains(ctxs):
+    from paper_2011_07209_gb300 import exx
+    cl, _ = ctxs
+    # R_PE = 7 bohr at 0.2 bohr spacing needs about 290 KB per CTA: the one-CTA solver runs
+    ws = synth.water_cell(np.diag([20.0] * 3), (100, 100, 100), 2, 61)
+    p = exx.make_params(r_pair=7.0, r_pe=7.0, r_me=8.0, tol=1e-9, precision=exx.MIXED)
+    g = _run(cl, ws, p, want_d=False)
+    assert g["info"]["cluster"] == 1 and g["status"] == 0
+    o = oracle.exx(ws, oracle.make_params(r_pair=7.0, r_pe=7.0, r_me=8.0, tol=1e-9), want_d=False)
+    assert g["e_xx"] == pytest.approx(o["e_xx"], rel=1e-7)
