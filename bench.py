@@ -125,6 +125,25 @@ def kernel_sha():
     return h.hexdigest()
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of the water64 cell solved by `rank`: every rank solves its own
+    independent cell (weak scaling), rank 0 the seed of the single-GPU run."""
+    return 7209 + 2 + 1000 * rank
+
+
+def reduce_over_ranks(elapsed_ms: float, n_pairs: int, dist, device):
+    """The slowest rank's timed region and the pairs of all ranks (one all-reduce
+    each; the only collectives of a multi-rank run)."""
+    if dist is None:
+        return elapsed_ms, n_pairs
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(n_pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(n.item()))
+
+
 def algorithmic_bytes(n_pairs, total_iter, total_refine, n_pe, n_me, s):
     """Bytes the pair solver must move per launch:
     CG: 7 N_PE s per iteration (x, r, p read + written, p read by the stencil);
@@ -200,7 +219,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     c = synth.CONFIGS[2]
-    seed = synth.SEED_BASE + 2 + 1000 * rank       # independent cell per rank (weak scaling)
+    seed = rank_seed(rank)       # independent cell per rank (weak scaling)
     ws = synth.water_cell(c["lattice"], c["n"], c["n_mol"], seed)
     if args.subset > 0:
         ws = ws.subset(args.subset)
@@ -241,13 +260,9 @@ def run_gpu(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    elapsed = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed, all_pairs = reduce_over_ranks(ev0.elapsed_time(ev1), n_pairs, dist, "cuda")
     ms_step = elapsed / args.steps
-    value = world * n_pairs * args.steps / (elapsed / 1e3)
+    value = all_pairs * args.steps / (elapsed / 1e3)
 
     # roofline of the dominant kernel (the persistent pair solver)
     s_bytes = 4.0
@@ -282,10 +297,10 @@ def run_gpu(args, rank, world, local_rank):
             exx.solve(ctx, cr.plan, ws.lattice, ws.n, orb, res, stream=sh)
         e1.record(stream)
         torch.cuda.synchronize()
-        et = e0.elapsed_time(e1) / n_e2e
+        et, e2e_pairs = reduce_over_ranks(e0.elapsed_time(e1) / n_e2e, res.n_pairs, dist, "cuda")
         h2d = phi_h.nbytes + cen_h.nbytes + lo_h.nbytes + dlo_h.nbytes
         d2h = dxx_h.nbytes + 19 * 8
-        e2e = {"value": world * res.n_pairs / (et / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_pairs / (et / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": et}
 
     cpu = None
