@@ -224,6 +224,8 @@ def run_gpu(args, rank, world, local_rank):
     if args.subset > 0:
         ws = ws.subset(args.subset)
     ctx = exx.Context(local_rank)
+    if args.solver == "cluster":
+        ctx.set_solver(exx.SOLVER_CLUSTER)
     p = exx.make_params(r_pair=c["r_pair"], r_pe=c["r_pe"], r_me=c["r_me"], tol=c["tol"], precision=exx.MIXED)
     cr = driver.prepare(ctx, ws, p, device=local_rank)
     stream = torch.cuda.current_stream()
@@ -316,11 +318,12 @@ def run_gpu(args, rank, world, local_rank):
                        "pairs_per_step": n_pairs, "n_pe": info["n_pe_pair"],
                        "n_me": info["n_me_pair"], "n_stcl": info["n_stcl"],
                        "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_fp64_residuals": tot_ref / max(n_pairs, 1),
-                       "ctas": info["ctas"], "threads": info["threads"],
+                       "ctas": info["ctas"], "threads": info["threads"], "ctas_per_pair": info["cluster"],
                        "l2": "inputs larger than L2 (orbital boxes 512 MB, D_xx 3.5 GB per step)",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair_solve<float>",
+                         "frac": achieved / peak, "traffic": traffic if args.solver == "cta" else None,
+                         "kernel": "k_pair_solve<float>" if args.solver == "cta" else "k_pair_solve_cluster",
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_solve,
                          "peak_kind": f"{peak_kind} HBM copy bandwidth"},
             "clocks": clocks,
@@ -454,6 +457,8 @@ def main():
                     help="water64 is the headline workload; the others print their own line")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="for --workload other than water64")
     ap.add_argument("--cold", action="store_true", help="trajectory256 without warm-started CG")
+    ap.add_argument("--solver", default="cta", choices=["cta", "cluster"],
+                    help="mixed-precision pair solver: one CTA per pair (default) or one 16-CTA cluster per pair")
     ap.add_argument("--subset", type=int, default=0,
                     help="solve only the pairs of the first K MLWFs (a small case of the same cell for profiling)")
     args = ap.parse_args()

@@ -707,7 +707,10 @@ __device__ __forceinline__ void update_group(float *__restrict__ rf, float *__re
     st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
 }
 
-constexpr int kSweepChunkGroups = 8;   // groups per thread between two CTA barriers of the sweep
+#ifndef EXX_SWEEP_GROUPS
+#define EXX_SWEEP_GROUPS 8
+#endif
+constexpr int kSweepChunkGroups = EXX_SWEEP_GROUPS;   // groups per thread between two CTA barriers of the sweep
 constexpr int kMaxSweepChunks = 512;   // chunks the one-sweep path can order
 
 // Mixed-precision Poisson solve of one pair in ONE sweep over the vectors per
@@ -733,8 +736,10 @@ constexpr int kMaxSweepChunks = 512;   // chunks the one-sweep path can order
 // runs, with one CTA barrier per chunk.  The stencil then reads p and r just
 // written by the update (cache-resident), and every vector crosses HBM once
 // per iteration: r, e, p, q read, r, e, p, q written.
+// Inlined into the kernel: as a separate function its parameter block lives in
+// local memory and is re-read inside the loop (measured 6 % slower).
 template <int FDN>
-__device__ __noinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
+__device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
 {
     const SetDev &S = *cg.S;
     const SmemCell &sm = *cg.sm;
