@@ -118,7 +118,14 @@ typedef struct {
                             /* previous MD step of Sec. III B 2.  The plan keeps one FP32    */
                             /* solution per pair (2 x n_pairs x N_PE x 4 bytes of device     */
                             /* memory).  The stopping rule is unchanged (|b - A v| <= tol |b|). */
-                            /* 0: every CG starts from v = 0.                                 */
+                            /* 0: every CG starts from v = 0 (or the multipole guess).        */
+    int guess;              /* 1 (default of the Python binding): a pair's CG without a warm */
+                            /* start begins from the free-space potential of rho_ij on PE,   */
+                            /* built from its multipole moments in radial bins (the far     */
+                            /* field of Eq. me continued inside), which removes about a      */
+                            /* quarter of the iterations; 0: from v = 0.  Only the starting  */
+                            /* point changes: the stopping rule and the solution do not.     */
+                            /* The cluster solver (exx_ctx_set_solver) ignores it.           */
 } exx_params;
 
 typedef struct {

@@ -119,6 +119,9 @@ struct exx_plan {
     PairOut *d_out = nullptr;
     // warm start (params.warm_start): solutions of the last solve, one FP32 vector per pair
     int32_t *d_inv[2] = {};           // dense-box offset -> PE index of each set
+    int32_t *d_gs_perm[2] = {}, *d_gs_bstart[2] = {};   // radial bins of the starting guess
+    uint8_t *d_gs_bin[2] = {};
+    float *d_gs_S32[2] = {};
     // row partitions for the cluster path (mixed precision)
     ClusterPart cpart[2];
     bool cl_ok[2] = {false, false};
@@ -148,6 +151,7 @@ static int check_params(const exx_params *p)
     if (p->stress_mode < EXX_STRESS_FULL || p->stress_mode > EXX_STRESS_CUBIC) return EXX_ERR_ARG;
     if (p->warm_start != 0 && p->warm_start != 1) return EXX_ERR_ARG;
     if (p->frozen < 0 || p->frozen > 2) return EXX_ERR_ARG;
+    if (p->guess != 0 && p->guess != 1) return EXX_ERR_ARG;
     return EXX_OK;
 }
 
@@ -173,6 +177,10 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_halo_off[s]);
         dev_free(p->d_groups[s]);
         dev_free(p->d_inv[s]);
+        dev_free(p->d_gs_perm[s]);
+        dev_free(p->d_gs_bstart[s]);
+        dev_free(p->d_gs_bin[s]);
+        dev_free(p->d_gs_S32[s]);
         dev_free(p->d_cl_cta[s]);
         dev_free(p->d_cl_rows[s]);
         dev_free(p->d_cl_grc[s]);
@@ -263,7 +271,10 @@ static int build_geometry(exx_plan *p)
         if ((e = dev_alloc(&p->d_S64[s], (size_t)o.n_pe * kNlm)) ||
             (e = dev_alloc(&p->d_S32[s], (size_t)o.n_pe * kNlm)) ||
             (e = dev_alloc(&p->d_T64[s], (size_t)(o.n_me - o.n_pe) * kNlm)) ||
-            (e = dev_alloc(&p->d_T32[s], (size_t)(o.n_me - o.n_pe) * kNlm)))
+            (e = dev_alloc(&p->d_T32[s], (size_t)(o.n_me - o.n_pe) * kNlm)) ||
+            (e = dev_alloc(&p->d_gs_perm[s], (size_t)o.n_pe)) || (e = dev_alloc(&p->d_gs_bstart[s], kGuessBins + 1)) ||
+            (e = dev_alloc(&p->d_gs_bin[s], (size_t)o.n_pe)) ||
+            (e = dev_alloc(&p->d_gs_S32[s], (size_t)o.n_pe * kNlm)))
             return e;
     }
     if ((e = upload_layouts(p))) return e;
@@ -316,6 +327,39 @@ static int update_metric(exx_plan *p, const exx_cell &cell)
     return EXX_OK;
 }
 
+// Radial bins of the PE points for the multipole starting guess, for the
+// current cell: bin = floor(kGuessBins |r-bar| / R_PE), points sorted by bin.
+static int upload_guess_bins(exx_plan *p)
+{
+    const double rpe[2] = {p->params.r_pe_self, p->params.r_pe_pair};
+    for (int s = 0; s < 2; ++s) {
+        const OffsetSet &o = p->off[s];
+        const int n = o.n_pe;
+        if (n == 0 || !p->d_gs_perm[s]) continue;
+        std::vector<uint8_t> bin(n);
+        std::vector<int32_t> count(kGuessBins + 1, 0), perm(n);
+        for (int k = 0; k < n; ++k) {
+            double r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double x = 0.0;
+                for (int al = 0; al < 3; ++al) x += p->metric.h[a][al] * o.m[3 * k + al] / p->metric.n[al];
+                r2 += x * x;
+            }
+            const int b = (int)std::min<double>(kGuessBins - 1, std::sqrt(r2) / rpe[s] * kGuessBins);
+            bin[k] = (uint8_t)std::max(0, b);
+            count[bin[k] + 1]++;
+        }
+        for (int b = 0; b < kGuessBins; ++b) count[b + 1] += count[b];
+        std::vector<int32_t> fill(count.begin(), count.end() - 1);
+        for (int k = 0; k < n; ++k) perm[fill[bin[k]]++] = k;
+        CK(cudaMemcpy(p->d_gs_perm[s], perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->d_gs_bstart[s], count.data(), 4 * (size_t)(kGuessBins + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->d_gs_bin[s], bin.data(), (size_t)n, cudaMemcpyHostToDevice));
+
+    }
+    return EXX_OK;
+}
+
 static void fill_celldev(const exx_plan *p, CellDev &C)
 {
     std::memset(&C, 0, sizeof(C));
@@ -351,6 +395,7 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
     C.precision = p->params.precision;
     C.r_pair2 = p->params.r_pair * p->params.r_pair;
     C.stress_mode = p->params.stress_mode;
+    C.guess = p->params.guess;
     for (int s = 0; s < 2; ++s) {
         const SetLayout &L = p->lay[s];
         SetDev &S = C.set[s];
@@ -374,6 +419,10 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
             S.rstride[d] = L.rstride[d];
             S.d2[d] = d < p->stencil.ndir ? p->stencil.dir[d][2] : 0;
         }
+        S.gs_perm = p->d_gs_perm[s];
+        S.gs_bstart = p->d_gs_bstart[s];
+        S.gs_bin = p->d_gs_bin[s];
+        S.gs_S32 = p->d_gs_S32[s];
         S.cl_cta = p->cl_ok[s] ? p->d_cl_cta[s] : nullptr;
         S.cl_rows = p->d_cl_rows[s];
         S.cl_grc = p->d_cl_grc[s];
@@ -461,6 +510,8 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
     o += vecb;
     s.off_e = o + 128;
     o += vecb;
+    s.off_gs = o + 128;
+    o += align256(2 * kGuessBins * kNlm * 4 + 256);
     s.slot_bytes = o;
     s.n_slots = n_slots;
     const size_t need = s.slot_bytes * (size_t)n_slots;
@@ -765,6 +816,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
         const exx_orbitals &o = orbs[c];
         exx_result &r = res[c];
         CellDev &C = ctx->h_cells[qi];
+        if (!p->tables_valid && (e = upload_guess_bins(p))) return e;   // radial bins for the current cell
         fill_celldev(p, C);
         C.n_orb = o.n_orb;
         for (int a = 0; a < 3; ++a) C.box[a] = o.box[a];
@@ -839,6 +891,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
             const SetLayout &L = p->lay[s];
             CK(launch_tables(ctx->d_cells + qi, s, L.n_pe + L.n_shell, p->d_S64[s], p->d_S32[s], p->d_T64[s],
                              p->d_T32[s], stream));
+            CK(launch_gather_rows(p->d_S32[s], p->d_gs_perm[s], L.n_pe, p->d_gs_S32[s], stream));
         }
         p->tables_valid = true;
     }

@@ -4,6 +4,7 @@
 
 namespace exx {
 
+constexpr int kGuessBins = 64;   // radial bins of the multipole starting guess
 constexpr int kNlm = 49;   // (lmax + 1)^2 for lmax = 6; tables are padded to this
 
 // Geometry of one subdomain kind (self pairs or non-self pairs) of one cell.
@@ -21,6 +22,11 @@ struct SetDev {
     int n_groups;
     int rstride[6];                // dstride without the last-axis component
     int d2[6];                     // last-axis component of each direction
+    // radial bins of the PE points (multipole starting guess): points sorted by bin
+    const int32_t *gs_perm;        // [n_pe] PE index of the sorted points
+    const int32_t *gs_bstart;      // [kGuessBins + 1] first sorted point of each bin
+    const uint8_t *gs_bin;         // [n_pe] bin of each PE point
+    const float *gs_S32;           // [n_pe][kNlm] S32 rows in sorted order
     // row partition over a cluster of CTAs (cluster path; cl_cta == NULL: not available)
     const int32_t *cl_cta;         // [nc][8]: G0, G1, K0, K1, rows, p_floats
     const int32_t *cl_rows;        // [B0 * B1][2]: owner rank (-2 halo-only row, -1 unused), offset of column 0
@@ -70,6 +76,7 @@ struct CellDev {
     int row_base;
     int cell_index;
     int stress_mode;               // 2: simple-cubic shortcut, the sigma integrals are skipped
+    int guess;                     // 1: CG starts from the free-space multipole potential
     // warm start: initial guesses from the previous solve of the same plan
     const int32_t *warm_map;       // [n_orb][n_orb] index of pair (i, j) in warm_rows, -1 none; NULL: cold
     const PairRec *warm_rows;

@@ -429,7 +429,7 @@ __device__ double residual_pass(const SetDev &S, const double *__restrict__ vbox
 struct SlotWork {
     char *base;
     size_t slot_bytes;
-    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e;
+    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e, off_gs;
 };
 
 // Shared per-CTA state.
@@ -910,6 +910,117 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
     }
 }
 
+
+// Starting guess of the CG: the free-space potential of rho on the PE points,
+//   v(r) = sum_lm 4 pi / (2l+1) Y_lm(r^) [ r^-(l+1) q<_lm(r) + r^l q>_lm(r) ],
+// q<_lm(r) = sum_{|r'| < r} rho r'^l Y_lm dV, q>_lm(r) = sum_{|r'| > r} rho r'^-(l+1) Y_lm dV,
+// with |r'| < r decided by radial bin (half of the point's own bin on each side).
+// Outside PE this is the far field of Eq. me, which is why it is close to the
+// solution of Eq. pe; it only sets where CG starts, not what it converges to.
+// gs: [2][kGuessBins][kNlm] scratch of the CTA.
+__device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 7, without branches
+{
+    const float r2 = ri * ri, r4 = r2 * r2, r8 = r4 * r4;
+    return ri * ((l & 1) ? r2 : 1.f) * ((l & 2) ? r4 : 1.f) * ((l & 4) ? r8 : 1.f);
+}
+__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, const double *__restrict__ rho,
+                                             double *__restrict__ vbox, float *__restrict__ gs)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int l0 = lane < 1 ? 0 : lane < 4 ? 1 : lane < 9 ? 2 : lane < 16 ? 3 : lane < 25 ? 4 : 5;   // l of lm = lane
+    const int l1 = lane + 32 < 36 ? 5 : 6;                                                          // l of lm = lane + 32
+    const bool has1 = lane + 32 < kNlm;
+    const int lane1 = has1 ? lane + 32 : lane;
+    float h[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
+    auto rinv_of = [&](int k) -> float {
+        int m0, m1, m2;
+        unpack_m(S.pe_m[k], m0, m1, m2);
+        const float x = h[0][0] * m0 + h[0][1] * m1 + h[0][2] * m2;
+        const float y = h[1][0] * m0 + h[1][1] * m1 + h[1][2] * m2;
+        const float z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
+        const float r2 = x * x + y * y + z * z;
+        return r2 > 0.f ? rsqrtf(r2) : 0.f;
+    };
+    float *A = gs, *B = gs + kGuessBins * kNlm;
+    const float dv = (float)C.dv;
+    // moments of each radial bin, one warp per bin (no atomics: the same sums on
+    // every run); warp w takes bins w and kGuessBins - 1 - w, a small and a large one
+    for (int u = warp; u < kGuessBins; u += nwarps) {
+        const int b = u < nwarps ? u : kGuessBins - 1 - (u - nwarps);
+        const int k0 = S.gs_bstart[b], k1 = S.gs_bstart[b + 1];
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        for (int x = k0; x < k1; x += 32) {
+            const bool live = x + lane < k1;
+            const int kk = S.gs_perm[live ? x + lane : x];
+            const float rl = live ? (float)rho[kk] : 0.f;
+            const float ri = rinv_of(kk);
+            const int xq = min(32, k1 - x);
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const float rp = __shfl_sync(0xffffffffu, rl, q);
+                const float rip = __shfl_sync(0xffffffffu, ri, q);
+                const float *row = S.gs_S32 + (size_t)(x + min(q, xq - 1)) * kNlm;   // rows in sorted order
+                const float s0 = row[lane], s1 = row[lane1];
+                a0 += rp * s0;
+                a1 += rp * s1;
+                b0 += rp * s0 * rinv_pow(rip, l0);
+                b1 += rp * s1 * rinv_pow(rip, l1);
+            }
+        }
+        A[b * kNlm + lane] = a0 * dv;
+        B[b * kNlm + lane] = b0 * dv;
+        if (has1) {
+            A[b * kNlm + lane + 32] = a1 * dv;
+            B[b * kNlm + lane + 32] = b1 * dv;
+        }
+    }
+    __syncthreads();
+    // inner sums from below, outer sums from above, half of the own bin each
+    if (tid < 2 * kNlm) {
+        const int lm = tid % kNlm;
+        float acc = 0.f;
+        if (tid < kNlm) {
+            for (int b = 0; b < kGuessBins; ++b) {
+                const float a = A[b * kNlm + lm];
+                A[b * kNlm + lm] = acc + 0.5f * a;
+                acc += a;
+            }
+        } else {
+            for (int b = kGuessBins - 1; b >= 0; --b) {
+                const float a = B[b * kNlm + lm];
+                B[b * kNlm + lm] = acc + 0.5f * a;
+                acc += a;
+            }
+        }
+    }
+    __syncthreads();
+    // v at every PE point: lanes carry lm, the warp sums them
+    const float c0 = 12.566370614359172f / (2 * l0 + 1), c1 = has1 ? 12.566370614359172f / (2 * l1 + 1) : 0.f;
+    const int nchunk = (S.n_pe + 31) >> 5;
+    for (int ch = warp; ch < nchunk; ch += nwarps) {
+        const int k0 = ch << 5;
+        const int cnt = min(32, S.n_pe - k0);
+        const int kl = k0 + min(lane, cnt - 1);
+        const float ri = rinv_of(kl);
+        const int bl = (int)S.gs_bin[kl];
+        float mine = 0.f;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const float rip = __shfl_sync(0xffffffffu, ri, q);
+            const int b = __shfl_sync(0xffffffffu, bl, q);
+            const float *row = S.S32 + (size_t)(k0 + min(q, cnt - 1)) * kNlm;
+            float t = c0 * row[lane] * (rinv_pow(rip, l0) * A[b * kNlm + lane] + B[b * kNlm + lane]) +
+                      c1 * row[lane1] * (rinv_pow(rip, l1) * A[b * kNlm + lane1] + B[b * kNlm + lane1]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == q) mine = t;
+        }
+        if (lane < cnt) vbox[S.pe_off[k0 + lane]] = (double)mine;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
                                                                  SlotWork W, int inner_shift)
@@ -981,28 +1092,37 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         {
             double a0 = 0.0, a1 = 0.0;
             const int nchunk = (S.n_pe + 31) >> 5;
+            // 32 points per step (rows past the end repeat the last one with weight 0),
+            // unrolled so that the table rows of several points are in flight at once
+            const int lane1 = lane + 32 < kNlm ? lane + 32 : lane;
+            const float sel1 = lane + 32 < kNlm ? 1.f : 0.f;
             for (int ch = warp; ch < nchunk; ch += nwarps) {
                 const int k0 = ch << 5;
                 const double rl = (k0 + lane < S.n_pe) ? rho[k0 + lane] : 0.0;
-                const int cnt = min(32, S.n_pe - k0);
+                const int last = min(32, S.n_pe - k0) - 1;
                 if (mixed) {
                     float f0 = 0.f, f1 = 0.f;
                     const float rlf = (float)rl;
-                    for (int p = 0; p < cnt; ++p) {
+#pragma unroll 8
+                    for (int p = 0; p < 32; ++p) {
                         const float rp = __shfl_sync(0xffffffffu, rlf, p);
-                        const float *row = S.S32 + (size_t)(k0 + p) * kNlm;
+                        const float *row = S.S32 + (size_t)(k0 + min(p, last)) * kNlm;
                         f0 += rp * row[lane];
-                        if (lane + 32 < kNlm) f1 += rp * row[lane + 32];
+                        f1 += rp * row[lane1];
                     }
                     a0 += f0;
-                    a1 += f1;
+                    a1 += sel1 * f1;
                 } else {
-                    for (int p = 0; p < cnt; ++p) {
+                    double f0 = 0.0, f1 = 0.0;
+#pragma unroll 4
+                    for (int p = 0; p < 32; ++p) {
                         const double rp = __shfl_sync(0xffffffffu, rl, p);
-                        const double *row = S.S64 + (size_t)(k0 + p) * kNlm;
-                        a0 += rp * row[lane];
-                        if (lane + 32 < kNlm) a1 += rp * row[lane + 32];
+                        const double *row = S.S64 + (size_t)(k0 + min(p, last)) * kNlm;
+                        f0 += rp * row[lane];
+                        f1 += rp * row[lane1];
                     }
+                    a0 += f0;
+                    a1 += sel1 * f1;
                 }
             }
             qpart[warp][lane] = a0;
@@ -1071,6 +1191,12 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 }
                 vbox[S.pe_off[k]] = v;
             }
+            __syncthreads();
+            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            rr2 = rnorm * rnorm;
+            ++refine;
+        } else if (C.guess && bn > 0.0 && S.gs_perm) {
+            multipole_guess(S, C, rho, vbox, reinterpret_cast<float *>(slot + W.off_gs));
             __syncthreads();
             rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
             rr2 = rnorm * rnorm;
@@ -2073,6 +2199,24 @@ cudaError_t launch_tables(const CellDev *cell, int which, int n_points, double *
     return cudaGetLastError();
 }
 
+// dst[j] = src[perm[j]], rows of kNlm floats (the solid-harmonic table in radial-bin order)
+__global__ void k_gather_rows(const float *__restrict__ src, const int32_t *__restrict__ perm, int n,
+                              float *__restrict__ dst)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (long long)n * kNlm) {
+        const int j = (int)(i / kNlm), lm = (int)(i % kNlm);
+        dst[i] = src[(size_t)perm[j] * kNlm + lm];
+    }
+}
+
+cudaError_t launch_gather_rows(const float *src, const int32_t *perm, int n, float *dst, cudaStream_t s)
+{
+    const long long total = (long long)n * kNlm;
+    if (total > 0) k_gather_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, perm, n, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pair_list(const CellDev *cells, int n_cells, int n_rows, const ListDev &L, cudaStream_t s)
 {
     if (n_rows > 0) k_pair_rows<<<n_rows, kRowThreads, 0, s>>>(cells, n_cells, L, 0);
@@ -2094,6 +2238,7 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
     W.off_r = slots.off_r;
     W.off_q = slots.off_q;
     W.off_e = slots.off_e;
+    W.off_gs = slots.off_gs;
     if (mixed) k_pair_solve<float><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     else k_pair_solve<double><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     return cudaGetLastError();

@@ -21,11 +21,14 @@ struct SolveSlots {
     char *base;
     size_t slot_bytes;
     size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e;
+    size_t off_gs;   // 2 kGuessBins kNlm floats: binned moments of the starting guess
     int n_slots;
 };
 
 cudaError_t launch_tables(const CellDev *cell, int which, int n_points, double *S64, float *S32, double *T64,
                           float *T32, cudaStream_t s);
+// dst[j][:] = src[perm[j]][:] for rows of kNlm floats
+cudaError_t launch_gather_rows(const float *src, const int32_t *perm, int n, float *dst, cudaStream_t s);
 cudaError_t launch_pair_list(const CellDev *cells, int n_cells, int n_rows, const ListDev &L, cudaStream_t s);
 cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlots &slots, bool mixed,
                          int inner_shift, cudaStream_t s);

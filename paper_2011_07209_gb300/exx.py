@@ -39,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("r_pair", C.c_double), ("r_pe_self", C.c_double), ("r_pe_pair", C.c_double),
                 ("r_me_self", C.c_double), ("r_me_pair", C.c_double), ("cg_tol", C.c_double),
                 ("fd_order", C.c_int), ("lmax", C.c_int), ("cg_max_iter", C.c_int), ("nq", C.c_int),
-                ("precision", C.c_int), ("frozen", C.c_int), ("stress_mode", C.c_int), ("warm_start", C.c_int)]
+                ("precision", C.c_int), ("frozen", C.c_int), ("stress_mode", C.c_int), ("warm_start", C.c_int),
+                ("guess", C.c_int)]
 
 
 class Orbitals(C.Structure):
@@ -129,7 +130,8 @@ def make_cell(lattice, n) -> Cell:
 
 
 def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, tol=1e-9, fd_order=3, lmax=6,
-                max_iter=20000, nq=15, precision=MIXED, frozen=False, stress_mode=0, warm_start=False) -> Params:
+                max_iter=20000, nq=15, precision=MIXED, frozen=False, stress_mode=0, warm_start=False,
+                guess=True) -> Params:
     p = Params()
     p.r_pair = r_pair
     p.r_pe_pair = r_pe
@@ -145,6 +147,7 @@ def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, 
     p.frozen = int(frozen)   # 0, 1 (offsets frozen) or 2 (offsets and aux directions frozen)
     p.stress_mode = int(stress_mode)
     p.warm_start = int(bool(warm_start))
+    p.guess = int(bool(guess))
     return p
 
 

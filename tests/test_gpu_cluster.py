@@ -1,5 +1,7 @@
 """GPU: the cluster pair solver (EXX_SOLVER_CLUSTER), which keeps each pair's
-FP32 CG state in the distributed shared memory of a 16-CTA cluster.
+FP32 CG state in the distributed shared memory of a 16-CTA cluster.  It starts
+each CG from zero (or a warm start), so the comparisons here run both solvers
+without the multipole starting guess.
 
 It must agree with the oracle on small cells (cubic, triclinic with the
 37-point stencil), with the one-CTA solver on the full 64-molecule cell and
@@ -52,7 +54,7 @@ def test_cluster_solver_small_cubic_cell(ctxs):
     from paper_2011_07209_gb300 import exx
     cl, _ = ctxs
     ws = synth.make_config(1)
-    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED)
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, guess=False)
     g = _run(cl, ws, p)
     assert g["info"]["cluster"] == 16 and g["status"] == 0
     o = oracle.exx(ws, oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10), dbox=g["dbox"],
@@ -65,7 +67,7 @@ def test_cluster_solver_triclinic_37_point_stencil(ctxs):
     cl, _ = ctxs
     lat = 14.0 * np.array([[1.0, 0.0, 0.0], [0.1, 1.0, 0.0], [0.05, -0.08, 1.0]])
     ws = synth.water_cell(lat, (56, 56, 56), 3, 5)
-    p = exx.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10, precision=exx.MIXED)
+    p = exx.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10, precision=exx.MIXED, guess=False)
     g = _run(cl, ws, p)
     assert g["info"]["cluster"] == 16 and g["n_stcl"] == 37
     o = oracle.exx(ws, oracle.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10), dbox=g["dbox"],
@@ -77,7 +79,7 @@ def test_cluster_matches_cta_solver_full_size(ctxs):
     from paper_2011_07209_gb300 import exx
     cl, cta = ctxs
     ws = synth.make_config(2)
-    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, precision=exx.MIXED)
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, precision=exx.MIXED, guess=False)
     a = _run(cl, ws, p, want_d=True)
     b = _run(cta, ws, p, want_d=True)
     assert a["info"]["cluster"] == 16 and b["info"]["cluster"] == 1
@@ -97,7 +99,8 @@ def test_cluster_warm_started_frozen_trajectory(ctxs):
     steps = synth.trajectory(ws0, 2, seed=synth.SEED_BASE + 51, strain_sigma=1e-3, centre_sigma=0.02)
     box = np.max([w.box for w in steps], axis=0)
     steps = [w.padded(box) for w in steps]
-    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, frozen=True, warm_start=True)
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, frozen=True, warm_start=True,
+                        guess=False)
     plan_cl = exx.Plan(cl, ws0.lattice, ws0.n, p, ws0.n_orb, box)
     plan_cta = exx.Plan(cta, ws0.lattice, ws0.n, p, ws0.n_orb, box)
     for k, ws in enumerate(steps):
@@ -114,7 +117,7 @@ def test_cluster_falls_back_for_large_subdomains(ctxs):
     cl, _ = ctxs
     # R_PE = 7 bohr at 0.2 bohr spacing needs about 290 KB per CTA: the one-CTA solver runs
     ws = synth.water_cell(np.diag([20.0] * 3), (100, 100, 100), 2, 61)
-    p = exx.make_params(r_pair=7.0, r_pe=7.0, r_me=8.0, tol=1e-9, precision=exx.MIXED)
+    p = exx.make_params(r_pair=7.0, r_pe=7.0, r_me=8.0, tol=1e-9, precision=exx.MIXED, guess=False)
     g = _run(cl, ws, p, want_d=False)
     assert g["info"]["cluster"] == 1 and g["status"] == 0
     o = oracle.exx(ws, oracle.make_params(r_pair=7.0, r_pe=7.0, r_me=8.0, tol=1e-9), want_d=False)

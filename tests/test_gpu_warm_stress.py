@@ -40,7 +40,8 @@ def test_warm_start_matches_cold_start_with_fewer_iterations(ctx, precision):
     from paper_2011_07209_gb300 import driver, exx
     lat0, steps = _trajectory(3)
     prec = exx.FP64 if precision == "fp64" else exx.MIXED
-    kw = dict(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=prec, frozen=True)
+    # against a CG that starts from zero (no multipole guess)
+    kw = dict(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=prec, frozen=True, guess=False)
     p_cold = exx.make_params(**kw)
     p_warm = exx.make_params(**kw, warm_start=True)
     n_orb, box, n = steps[0].n_orb, steps[0].box, steps[0].n
@@ -109,3 +110,30 @@ def test_cubic_shortcut_rejects_other_cells(ctx):
     with pytest.raises(exx.ExxError) as ei:
         driver.run(ctx, cr)
     assert ei.value.code == exx.ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multipole_guess_same_results_fewer_iterations(ctx, precision):
+    # the starting point is the free-space multipole potential of rho_ij: CG ends at the
+    # same solution (same stopping rule) in fewer iterations
+    from paper_2011_07209_gb300 import driver, exx
+    ws = synth.make_config(1)
+    prec = exx.FP64 if precision == "fp64" else exx.MIXED
+    out = {}
+    for g in (False, True):
+        p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=prec, guess=g)
+        cr = driver.prepare(ctx, ws, p)
+        out[g] = driver.run(ctx, cr)
+        out[g]["dxx"] = cr.dxx.cpu().numpy()
+        out[g]["dbox"], out[g]["dbox_lo"] = cr.dbox, cr.dbox_lo_np
+    a, b = out[True], out[False]
+    assert a["status"] == 0 and b["status"] == 0
+    assert a["e_xx"] == pytest.approx(b["e_xx"], rel=1e-8)
+    assert np.abs(a["stress"] - b["stress"]).max() < 1e-10
+    assert np.abs(a["dxx"] - b["dxx"]).max() < 1e-8
+    assert a["total_cg_iter"] < 0.9 * b["total_cg_iter"], (a["total_cg_iter"], b["total_cg_iter"])
+    o = oracle.exx(ws, oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10), dbox=a["dbox"],
+                   dbox_lo=a["dbox_lo"])
+    assert a["e_xx"] == pytest.approx(o["e_xx"], rel=1e-7 if precision == "mixed" else 1e-9)
+    assert np.abs(a["stress"] - o["stress"]).max() < 1e-8
+    assert np.abs(a["dxx"] - o["dxx"]).max() < 1e-6
