@@ -118,6 +118,9 @@ typedef struct {
                             /* previous MD step of Sec. III B 2.  The plan keeps one FP32    */
                             /* solution per pair (2 x n_pairs x N_PE x 4 bytes of device     */
                             /* memory).  The stopping rule is unchanged (|b - A v| <= tol |b|). */
+                            /* With guess = 1 the previous solution is kept only when its    */
+                            /* residual is at most 5 % of |b|; otherwise the pair starts     */
+                            /* from the multipole guess (large MD steps).                    */
                             /* 0: every CG starts from v = 0 (or the multipole guess).        */
     int guess;              /* 1 (default of the Python binding): a pair's CG without a warm */
                             /* start begins from the free-space potential of rho_ij on PE,   */

@@ -918,6 +918,8 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
 // Outside PE this is the far field of Eq. me, which is why it is close to the
 // solution of Eq. pe; it only sets where CG starts, not what it converges to.
 // gs: [2][kGuessBins][kNlm] scratch of the CTA.
+constexpr double kWarmAccept = 0.05;   // warm starts kept when |b - A v_prev| <= 5 % of |b|
+
 __device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 7, without branches
 {
     const float r2 = ri * ri, r4 = r2 * r2, r8 = r4 * r4;
@@ -1195,7 +1197,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
             rr2 = rnorm * rnorm;
             ++refine;
-        } else if (C.guess && bn > 0.0 && S.gs_perm) {
+            // a previous solution that the pair has moved away from starts worse than
+            // the multipole potential (typically 3-18 % of |b|): keep it only when close
+            if (C.guess && S.gs_perm && !(rnorm <= kWarmAccept * bn)) warm = -1;
+        }
+        if (warm < 0 && C.guess && bn > 0.0 && S.gs_perm) {
             multipole_guess(S, C, rho, vbox, reinterpret_cast<float *>(slot + W.off_gs));
             __syncthreads();
             rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));

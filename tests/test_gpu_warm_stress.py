@@ -137,3 +137,25 @@ def test_multipole_guess_same_results_fewer_iterations(ctx, precision):
     assert a["e_xx"] == pytest.approx(o["e_xx"], rel=1e-7 if precision == "mixed" else 1e-9)
     assert np.abs(a["stress"] - o["stress"]).max() < 1e-8
     assert np.abs(a["dxx"] - o["dxx"]).max() < 1e-6
+
+
+def test_warm_start_falls_back_to_multipole_guess_for_large_steps(ctx):
+    # centres moved by 0.15 bohr: previous solutions start worse than the multipole
+    # potential, so (guess on) most pairs start from the latter; results unchanged
+    from paper_2011_07209_gb300 import driver, exx
+    ws0 = synth.make_config(1)
+    steps = synth.trajectory(ws0, 2, seed=synth.SEED_BASE + 52, strain_sigma=1e-3, centre_sigma=0.15)
+    box = np.max([w.box for w in steps], axis=0)
+    steps = [w.padded(box) for w in steps]
+    kw = dict(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, frozen=True)
+    plan_w = exx.Plan(ctx, ws0.lattice, ws0.n, exx.make_params(**kw, warm_start=True), ws0.n_orb, box)
+    plan_g = exx.Plan(ctx, ws0.lattice, ws0.n, exx.make_params(**kw), ws0.n_orb, box)
+    for k, ws in enumerate(steps):
+        w = driver.run(ctx, driver.prepare(ctx, ws, exx.make_params(**kw, warm_start=True), plan=plan_w,
+                                           want_d=False))
+        g = driver.run(ctx, driver.prepare(ctx, ws, exx.make_params(**kw), plan=plan_g, want_d=False))
+        assert w["status"] == 0 and g["status"] == 0
+        assert w["e_xx"] == pytest.approx(g["e_xx"], rel=1e-8)
+        if k == 1:
+            assert w["n_warm"] < 0.5 * w["n_pairs"]
+            assert w["total_cg_iter"] < 1.1 * g["total_cg_iter"]
