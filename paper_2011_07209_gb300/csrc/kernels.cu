@@ -641,6 +641,25 @@ __device__ __forceinline__ void st4(float *p, float a, float b, float c, float d
 {
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
+#ifndef EXX_STREAM_HINTS
+#define EXX_STREAM_HINTS 0
+#endif
+__device__ __forceinline__ float4 ld4s(const float *p)
+{
+#if EXX_STREAM_HINTS
+    return __ldcs(reinterpret_cast<const float4 *>(p));
+#else
+    return ld4(p);
+#endif
+}
+__device__ __forceinline__ void st4s(float *p, float a, float b, float c, float d)
+{
+#if EXX_STREAM_HINTS
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(a, b, c, d));
+#else
+    st4(p, a, b, c, d);
+#endif
+}
 
 // q = -(L p) on the PE lanes of one aligned group (zero on the others), stored,
 // with the four products <p,q>, <q,q>, <r,q>, <r,p> of the group added to the
@@ -686,8 +705,8 @@ __device__ __forceinline__ void stencil_group(const float *__restrict__ pf, cons
     }
     const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
     const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
-    st4(qf + off, q0, q1, q2, q3);
-    const float4 r = ld4(rf + off);
+    st4s(qf + off, q0, q1, q2, q3);
+    const float4 r = ld4s(rf + off);
     df_add(apq, c.x * q0 + c.y * q1 + c.z * q2 + c.w * q3);
     df_add(aqq, q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
     df_add(arq, r.x * q0 + r.y * q1 + r.z * q2 + r.w * q3);
@@ -699,11 +718,11 @@ __device__ __forceinline__ void stencil_group(const float *__restrict__ pf, cons
 __device__ __forceinline__ void update_group(float *__restrict__ rf, float *__restrict__ ef, float *__restrict__ pf,
                                              const float *__restrict__ qf, int off, float alpha, float beta, DF &arr)
 {
-    const float4 r = ld4(rf + off), q = ld4(qf + off), p_ = ld4(pf + off), e = ld4(ef + off);
+    const float4 r = ld4(rf + off), q = ld4s(qf + off), p_ = ld4(pf + off), e = ld4s(ef + off);
     const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
     df_add(arr, r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
     st4(rf + off, r0, r1, r2, r3);
-    st4(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
+    st4s(ef + off, e.x + alpha * p_.x, e.y + alpha * p_.y, e.z + alpha * p_.z, e.w + alpha * p_.w);
     st4(pf + off, r0 + beta * p_.x, r1 + beta * p_.y, r2 + beta * p_.z, r3 + beta * p_.w);
 }
 
@@ -917,7 +936,7 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
 // with |r'| < r decided by radial bin (half of the point's own bin on each side).
 // Outside PE this is the far field of Eq. me, which is why it is close to the
 // solution of Eq. pe; it only sets where CG starts, not what it converges to.
-// gs: [2][kGuessBins][kNlm] scratch of the CTA.
+// gs: [2][kGuessBins][kNlm] scratch of the CTA (inner, outer moments per bin).
 constexpr double kWarmAccept = 0.05;   // warm starts kept when |b - A v_prev| <= 5 % of |b|
 
 __device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 7, without branches
@@ -925,8 +944,25 @@ __device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 
     const float r2 = ri * ri, r4 = r2 * r2, r8 = r4 * r4;
     return ri * ((l & 1) ? r2 : 1.f) * ((l & 2) ? r4 : 1.f) * ((l & 4) ? r8 : 1.f);
 }
-__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, const double *__restrict__ rho,
-                                             double *__restrict__ vbox, float *__restrict__ gs)
+
+__device__ __forceinline__ void pe_xyz(const SetDev &S, const float (*h)[3], int k, float &x, float &y, float &z)
+{
+    int m0, m1, m2;
+    unpack_m(S.pe_m[k], m0, m1, m2);
+    x = h[0][0] * m0 + h[0][1] * m1 + h[0][2] * m2;
+    y = h[1][0] * m0 + h[1][1] * m1 + h[1][2] * m2;
+    z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
+}
+
+// Multipole moments of rho per radial bin, one warp per bin over the
+// radius-sorted copy of the solid-harmonic table (no atomics: the same sums on
+// every run): gs gets the inner moments rho r^l Y_lm dV and the outer moments
+// rho r^-(l+1) Y_lm dV of each bin, and qpart[w] the FP64 sum of the inner
+// moments over warp w's bins.  The sum over the bins is the moment Q_lm of
+// Eq. mepole (up to dV), accumulated like the one-pass moments: FP32 over 32
+// points, FP64 beyond.
+__device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, const double *__restrict__ rho,
+                                         float *__restrict__ gs, double (*qpart)[kNlm])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int l0 = lane < 1 ? 0 : lane < 4 ? 1 : lane < 9 ? 2 : lane < 16 ? 3 : lane < 25 ? 4 : 5;   // l of lm = lane
@@ -936,49 +972,62 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
     float h[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
-    auto rinv_of = [&](int k) -> float {
-        int m0, m1, m2;
-        unpack_m(S.pe_m[k], m0, m1, m2);
-        const float x = h[0][0] * m0 + h[0][1] * m1 + h[0][2] * m2;
-        const float y = h[1][0] * m0 + h[1][1] * m1 + h[1][2] * m2;
-        const float z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
-        const float r2 = x * x + y * y + z * z;
-        return r2 > 0.f ? rsqrtf(r2) : 0.f;
-    };
     float *A = gs, *B = gs + kGuessBins * kNlm;
-    const float dv = (float)C.dv;
-    // moments of each radial bin, one warp per bin (no atomics: the same sums on
-    // every run); warp w takes bins w and kGuessBins - 1 - w, a small and a large one
+    const double dv = C.dv;
+    double w0 = 0.0, w1 = 0.0;
+    // warp w takes bins w and kGuessBins - 1 - w, a small and a large one
     for (int u = warp; u < kGuessBins; u += nwarps) {
         const int b = u < nwarps ? u : kGuessBins - 1 - (u - nwarps);
         const int k0 = S.gs_bstart[b], k1 = S.gs_bstart[b + 1];
-        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        double a0 = 0.0, a1 = 0.0;
+        float b0 = 0.f, b1 = 0.f;
         for (int x = k0; x < k1; x += 32) {
             const bool live = x + lane < k1;
             const int kk = S.gs_perm[live ? x + lane : x];
             const float rl = live ? (float)rho[kk] : 0.f;
-            const float ri = rinv_of(kk);
+            float px, py, pz;
+            pe_xyz(S, h, kk, px, py, pz);
+            const float r2 = px * px + py * py + pz * pz;
+            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
             const int xq = min(32, k1 - x);
+            float f0 = 0.f, f1 = 0.f;
 #pragma unroll 8
             for (int q = 0; q < 32; ++q) {
                 const float rp = __shfl_sync(0xffffffffu, rl, q);
                 const float rip = __shfl_sync(0xffffffffu, ri, q);
                 const float *row = S.gs_S32 + (size_t)(x + min(q, xq - 1)) * kNlm;   // rows in sorted order
                 const float s0 = row[lane], s1 = row[lane1];
-                a0 += rp * s0;
-                a1 += rp * s1;
+                f0 += rp * s0;
+                f1 += rp * s1;
                 b0 += rp * s0 * rinv_pow(rip, l0);
                 b1 += rp * s1 * rinv_pow(rip, l1);
             }
+            a0 += f0;
+            a1 += f1;
         }
-        A[b * kNlm + lane] = a0 * dv;
-        B[b * kNlm + lane] = b0 * dv;
+        A[b * kNlm + lane] = (float)(a0 * dv);
+        B[b * kNlm + lane] = (float)(b0 * dv);
         if (has1) {
-            A[b * kNlm + lane + 32] = a1 * dv;
-            B[b * kNlm + lane + 32] = b1 * dv;
+            A[b * kNlm + lane + 32] = (float)(a1 * dv);
+            B[b * kNlm + lane + 32] = (float)(b1 * dv);
         }
+        w0 += a0;
+        w1 += a1;
     }
-    __syncthreads();
+    qpart[warp][lane] = w0;
+    if (has1) qpart[warp][lane + 32] = w1;
+}
+
+// The guess itself from the bin moments of bin_moments: cumulative inner and
+// outer sums, then v at every PE point with r^l Y_lm from the Cartesian
+// recurrences of solid_harmonics in FP32.  Points are visited in radius order,
+// so the lanes of a warp share one or two bins and read the same moments.
+__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, double *__restrict__ vbox,
+                                             float *__restrict__ gs)
+{
+    __shared__ float cn[kNlm];   // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float *A = gs, *B = gs + kGuessBins * kNlm;
     // inner sums from below, outer sums from above, half of the own bin each
     if (tid < 2 * kNlm) {
         const int lm = tid % kNlm;
@@ -996,30 +1045,62 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
                 acc += a;
             }
         }
+    } else if (tid < 3 * kNlm) {
+        const int lm = tid - 2 * kNlm;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= lm) ++l;
+        const int m = lm - l * l - l;
+        float c = 0.f;
+        if (m >= 0) {
+            double ratio = 1.0;   // (l-m)!/(l+m)!
+            for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+            const double nlm = sqrt((2.0 * l + 1.0) / kFourPi * ratio);
+            c = (float)(m == 0 ? nlm : 1.4142135623730951 * nlm);
+        }
+        cn[lm] = c;
     }
     __syncthreads();
-    // v at every PE point: lanes carry lm, the warp sums them
-    const float c0 = 12.566370614359172f / (2 * l0 + 1), c1 = has1 ? 12.566370614359172f / (2 * l1 + 1) : 0.f;
-    const int nchunk = (S.n_pe + 31) >> 5;
-    for (int ch = warp; ch < nchunk; ch += nwarps) {
-        const int k0 = ch << 5;
-        const int cnt = min(32, S.n_pe - k0);
-        const int kl = k0 + min(lane, cnt - 1);
-        const float ri = rinv_of(kl);
-        const int bl = (int)S.gs_bin[kl];
-        float mine = 0.f;
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-            const float rip = __shfl_sync(0xffffffffu, ri, q);
-            const int b = __shfl_sync(0xffffffffu, bl, q);
-            const float *row = S.S32 + (size_t)(k0 + min(q, cnt - 1)) * kNlm;
-            float t = c0 * row[lane] * (rinv_pow(rip, l0) * A[b * kNlm + lane] + B[b * kNlm + lane]) +
-                      c1 * row[lane1] * (rinv_pow(rip, l1) * A[b * kNlm + lane1] + B[b * kNlm + lane1]);
+    float h[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
+    const int lmax = C.lmax;
+    for (int j = tid; j < S.n_pe; j += nt) {
+        const int kk = S.gs_perm[j];
+        const float *Ab = A + (int)S.gs_bin[kk] * kNlm, *Bb = B + (int)S.gs_bin[kk] * kNlm;
+        float x, y, z;
+        pe_xyz(S, h, kk, x, y, z);
+        const float r2 = x * x + y * y + z * z;
+        const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f, ri2 = ri * ri;
+        float v = 0.f;
+        float Am = 1.f, Bm = 0.f, dfact = 1.f, fm = ri;   // (x + iy)^m, (2m-1)!!, r^-(2m+1)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == q) mine = t;
+        for (int m = 0; m <= 6; ++m) {
+            if (m > 0) {
+                const float An = x * Am - y * Bm;
+                Bm = x * Bm + y * Am;
+                Am = An;
+                dfact *= (float)(2 * m - 1);
+                fm *= ri2;
+            }
+            float q1 = 0.f, q2 = 0.f, fl = fm;   // Q_{l-1}^m, Q_{l-2}^m, r^-(2l+1)
+#pragma unroll
+            for (int l = m; l <= 6; ++l) {
+                float q;
+                if (l == m) q = dfact;
+                else if (l == m + 1) q = (float)(2 * m + 1) * z * dfact;
+                else q = ((float)(2 * l - 1) * z * q1 - (float)(l + m - 1) * r2 * q2) * (1.f / (float)(l - m));
+                q2 = q1;
+                q1 = q;
+                if (l > m) fl *= ri2;
+                if (l <= lmax) {
+                    const int i0 = l * l + l;
+                    const float c = (12.566370614359172f / (float)(2 * l + 1)) * cn[i0 + m] * q;
+                    if (m == 0) v += c * (fl * Ab[i0] + Bb[i0]);
+                    else v += c * (Am * (fl * Ab[i0 + m] + Bb[i0 + m]) + Bm * (fl * Ab[i0 - m] + Bb[i0 - m]));
+                }
+            }
         }
-        if (lane < cnt) vbox[S.pe_off[k0 + lane]] = (double)mine;
+        vbox[S.pe_off[kk]] = (double)v;
     }
 }
 
@@ -1091,7 +1172,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         __syncthreads();
 
         // ---- multipole moments Q_lm = dV sum_PE rho r^l Y_lm (Eq. mepole) ----
-        {
+        float *gs = reinterpret_cast<float *>(slot + W.off_gs);
+        if (mixed && S.gs_perm) {
+            // by radial bin: the same pass gives the moments of the starting guess
+            bin_moments(S, C, rho, gs, qpart);
+        } else {
             double a0 = 0.0, a1 = 0.0;
             const int nchunk = (S.n_pe + 31) >> 5;
             // 32 points per step (rows past the end repeat the last one with weight 0),
@@ -1129,6 +1214,8 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             }
             qpart[warp][lane] = a0;
             if (lane + 32 < kNlm) qpart[warp][lane + 32] = a1;
+        }
+        {
             __syncthreads();
             if (tid < kNlm) {
                 double s = 0.0;
@@ -1202,7 +1289,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             if (C.guess && S.gs_perm && !(rnorm <= kWarmAccept * bn)) warm = -1;
         }
         if (warm < 0 && C.guess && bn > 0.0 && S.gs_perm) {
-            multipole_guess(S, C, rho, vbox, reinterpret_cast<float *>(slot + W.off_gs));
+            if (!mixed) {
+                bin_moments(S, C, rho, gs, qpart);
+                __syncthreads();
+            }
+            multipole_guess(S, C, vbox, gs);
             __syncthreads();
             rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
             rr2 = rnorm * rnorm;
@@ -1319,15 +1410,16 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                     if (s <= fdn) t += C.w1dx[al][s] * (vbox[off + s * st] - vbox[off - s * st]);
                 dxi[al] = t;
             }
+            // sum_PE m_alpha rho d_b v; the lattice Jacobian and 1/N_alpha are
+            // constant over the cell and applied to the nine sums once per pair
             int m0, m1, m2;
             unpack_m(S.pe_m[k], m0, m1, m2);
-            const double sb[3] = {(double)m0 / C.n[0], (double)m1 / C.n[1], (double)m2 / C.n[2]};
+            const double mb[3] = {(double)m0, (double)m1, (double)m2};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double dva = C.J[a][0] * dxi[0] + C.J[a][1] * dxi[1] + C.J[a][2] * dxi[2];
-                const double rdv = rk * dva;
+            for (int b = 0; b < 3; ++b) {
+                const double rd = rk * dxi[b];
 #pragma unroll
-                for (int al = 0; al < 3; ++al) acc[1 + 3 * a + al] += sb[al] * rdv;
+                for (int al = 0; al < 3; ++al) acc[1 + 3 * b + al] += mb[al] * rd;
             }
         }
         block_sum<10>(acc, red);
@@ -1385,7 +1477,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         if (tid == 0) {
             PairOut o;
             o.e = acc[0] * C.dv;
-            for (int k = 0; k < 9; ++k) o.sig[k] = acc[1 + k] * C.dv;
+            // sigma[a][alpha] = dV / N_alpha sum_b J[a][b] sum_PE m_alpha rho d_b v
+            for (int a = 0; a < 3; ++a)
+                for (int al = 0; al < 3; ++al)
+                    o.sig[3 * a + al] = (C.J[a][0] * acc[1 + al] + C.J[a][1] * acc[4 + al] + C.J[a][2] * acc[7 + al]) /
+                                        C.n[al] * C.dv;
             o.iters = iters;
             o.refine = refine;
             o.status = status ? status : (s_flag ? 7 : 0);
@@ -2083,13 +2179,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pair_solve_cluster(const
             }
             int m0, m1, m2;
             unpack_m(S.pe_m[k], m0, m1, m2);
-            const double sb[3] = {(double)m0 / C.n[0], (double)m1 / C.n[1], (double)m2 / C.n[2]};
+            const double mb[3] = {(double)m0, (double)m1, (double)m2};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double dva = C.J[a][0] * dxi[0] + C.J[a][1] * dxi[1] + C.J[a][2] * dxi[2];
-                const double rdv = rk * dva;
+            for (int b = 0; b < 3; ++b) {
+                const double rd = rk * dxi[b];
 #pragma unroll
-                for (int al = 0; al < 3; ++al) acc[1 + 3 * a + al] += sb[al] * rdv;
+                for (int al = 0; al < 3; ++al) acc[1 + 3 * b + al] += mb[al] * rd;
             }
         }
         __syncthreads();
@@ -2098,7 +2193,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pair_solve_cluster(const
         if (rank == 0 && tid == 0) {
             PairOut o;
             o.e = acc[0] * C.dv;
-            for (int k = 0; k < 9; ++k) o.sig[k] = acc[1 + k] * C.dv;
+            // sigma[a][alpha] = dV / N_alpha sum_b J[a][b] sum_PE m_alpha rho d_b v
+            for (int a = 0; a < 3; ++a)
+                for (int al = 0; al < 3; ++al)
+                    o.sig[3 * a + al] = (C.J[a][0] * acc[1 + al] + C.J[a][1] * acc[4 + al] + C.J[a][2] * acc[7 + al]) /
+                                        C.n[al] * C.dv;
             o.iters = iters;
             o.refine = refine;
             o.status = status ? status : (acc[10] > 0.0 ? 7 : 0);
