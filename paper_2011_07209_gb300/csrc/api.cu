@@ -512,6 +512,8 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
     o += vecb;
     s.off_gs = o + 128;
     o += align256(2 * kGuessBins * kNlm * 4 + 256);
+    s.off_b2 = o + 128;
+    o += align256(8 * npe_max + 256);
     s.slot_bytes = o;
     s.n_slots = n_slots;
     const size_t need = s.slot_bytes * (size_t)n_slots;

@@ -426,10 +426,115 @@ __device__ double residual_pass(const SetDev &S, const double *__restrict__ vbox
     return acc[0];
 }
 
+// ---------------------------------------------------------------------------
+// Normalised double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2,
+// 48 significant bits from FP32 operations (GB300 runs FP64 at 1/64 of the FP32
+// rate).  Knuth's TwoSum, Dekker's FastTwoSum and the FMA TwoProd are exact;
+// the sum and product below are the accurate double-word algorithms of
+// Joldes, Muller and Popescu (2017), relative error a few 2^-48.  Round-to-
+// nearest intrinsics throughout, so that no step is contracted into an FMA.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    return make_float2(s, __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb)));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b)   // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fadd_rn(b, -__fadd_rn(s, -a)));
+}
+__device__ __forceinline__ float2 two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 dw_add(float2 x, float2 y)
+{
+    const float2 s = two_sum(x.x, y.x), t = two_sum(x.y, y.y);
+    const float2 v = fast_two_sum(s.x, __fadd_rn(s.y, t.x));
+    return fast_two_sum(v.x, __fadd_rn(t.y, v.y));
+}
+__device__ __forceinline__ float2 dw_add_f(float2 x, float y)   // double-float + float
+{
+    const float2 s = two_sum(x.x, y);
+    return fast_two_sum(s.x, __fadd_rn(x.y, s.y));
+}
+__device__ __forceinline__ float2 dw_mul(float2 x, float2 y)
+{
+    const float ph = __fmul_rn(x.x, y.x);
+    float pl = __fmaf_rn(x.x, y.x, -ph);
+    pl = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, pl));
+    return fast_two_sum(ph, pl);
+}
+__device__ __forceinline__ float2 dw_split(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+// r = 4 pi rho + L v on PE in double-float arithmetic: v as (hi, lo) pairs in
+// the dense box, 4 pi rho as pairs per PE point, stencil weights as pairs.  The
+// error is a few 2^-48 of the sum of the magnitudes of the stencil terms (FP64:
+// 2^-53), far below the CG tolerance times |b|.  r is stored rounded to FP32,
+// the precision of the inner solve it restarts; returns sum r^2 in FP64.
+template <int FDN>
+__device__ __noinline__ double residual_df(const SetDev &S, const float2 *vb, const float2 *__restrict__ b2,
+                                           float *__restrict__ r32, const float2 (*cw)[8], float2 center,
+                                           const int *ds, int ndir, double *red)
+{
+    double acc[1] = {0.0};
+    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        float2 a = dw_mul(center, vb[off]);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (d < ndir) {
+                const int st = ds[d];
+#pragma unroll
+                for (int s_ = 1; s_ <= FDN; ++s_)
+                    a = dw_add(a, dw_mul(cw[d][s_], dw_add(vb[off + s_ * st], vb[off - s_ * st])));
+            }
+        }
+        a = dw_add(a, b2[k]);
+        const float r = __fadd_rn(a.x, a.y);
+        r32[k] = r;
+        acc[0] += (double)r * (double)r;
+    }
+    block_sum<1>(acc, red);
+    return acc[0];
+}
+__device__ __forceinline__ double residual_df_n(int fdn, const SetDev &S, const float2 *vb, const float2 *b2,
+                                                float *r32, const float2 (*cw)[8], float2 center, const int *ds,
+                                                int ndir, double *red)
+{
+    switch (fdn) {
+    case 1: return residual_df<1>(S, vb, b2, r32, cw, center, ds, ndir, red);
+    case 2: return residual_df<2>(S, vb, b2, r32, cw, center, ds, ndir, red);
+    case 3: return residual_df<3>(S, vb, b2, r32, cw, center, ds, ndir, red);
+    default: return residual_df<4>(S, vb, b2, r32, cw, center, ds, ndir, red);
+    }
+}
+
+// x * sc in FP32 for any FP64 scale sc (sc = m 2^e, x m rounded once, then an
+// exact power-of-two scaling), so that tiny residuals reach the O(1) frame.
+struct F32Scale {
+    float m;
+    int e;
+    __device__ float apply(float x) const { return ldexpf(__fmul_rn(x, m), e); }
+};
+__device__ __forceinline__ F32Scale f32_scale(double sc)
+{
+    int e;
+    const double m = frexp(sc, &e);
+    return {(float)m, e};
+}
+
 struct SlotWork {
     char *base;
     size_t slot_bytes;
-    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e, off_gs;
+    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e, off_gs, off_b2;
 };
 
 // Shared per-CTA state.
@@ -437,6 +542,8 @@ struct SmemCell {
     CellDev C;
     double cw64[6][8];
     float cw32[6][8];
+    float2 cwdf[6][8];   // cw64 as double-float pairs
+    float2 centerdf;
     double Q[kNlm];
     float Qf[kNlm];
     double center64;
@@ -456,6 +563,7 @@ struct CgMixed {
     int ndir, fdn, max_iter;
     double stop, bn, inner_red;
     double r0n;   // norm of the starting residual b - A v0 (the first frame)
+    const float2 *b2;   // 4 pi rho as double-float pairs (one-sweep path)
 };
 
 __device__ __noinline__ void cg_mixed(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
@@ -757,14 +865,75 @@ constexpr int kMaxSweepChunks = 512;   // chunks the one-sweep path can order
 // per iteration: r, e, p, q read, r, e, p, q written.
 // Inlined into the kernel: as a separate function its parameter block lives in
 // local memory and is re-read inside the loop (measured 6 % slower).
+// Scalars of a sweep-CG iteration, kept by thread 0 and broadcast through shared memory.
+struct SweepScalars {
+    double rr, rmax, S, pq;
+    float alpha, beta;
+    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+};
+
+// The reliable update of the sweep CG, out of line so that the registers of
+// the sweep loop do not depend on it: v += (e + alpha p) S in double-float, the
+// double-float true residual, and (unless it meets the tolerance) r restarted
+// in the frame of its new norm with p = r + gamma p, gamma keeping p
+// A-conjugate to the last direction (zero after a breakdown).  Returns true
+// when the true residual meets the tolerance.
+__device__ __noinline__ bool sweep_replace(const CgMixed &cg, SweepScalars &cs, float alpha, int act, double &rnorm)
+{
+    const SetDev &S = *cg.S;
+    const SmemCell &sm = *cg.sm;
+    float2 *vb = reinterpret_cast<float2 *>(cg.vbox);
+    float *r32 = reinterpret_cast<float *>(cg.r64);
+    float *__restrict__ pf = cg.pf;
+    float *__restrict__ rf = cg.rf;
+    const float *__restrict__ qf = cg.qf;
+    float *__restrict__ ef = cg.ef;
+    const int32_t *__restrict__ poff = S.pe_off;
+    const int npe = S.n_pe, tid = threadIdx.x, nt = blockDim.x;
+    const float2 S2 = dw_split(cs.S);
+    for (int k = tid; k < npe; k += nt) {
+        const int off = poff[k];
+        const float2 t = dw_add_f(two_prod(alpha, pf[off]), ef[off]);
+        vb[off] = dw_add(vb[off], dw_mul(t, S2));
+        ef[off] = 0.f;
+    }
+    __syncthreads();
+    rnorm = sqrt(residual_df_n(cg.fdn, S, vb, cg.b2, r32, sm.cwdf, sm.centerdf, sm.ds, cg.ndir, cg.red));
+    if (rnorm <= cg.stop) return true;
+    const F32Scale sc = f32_scale(1.0 / rnorm);
+    DF ab[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k = tid; k < npe; k += nt) {
+        const int off = poff[k];
+        const float r = sc.apply(r32[k]);
+        rf[off] = r;
+        df_fma(ab[0], r, r);
+        df_fma(ab[1], r, qf[off]);
+    }
+    block_sum_df<2>(ab, reinterpret_cast<float2 *>(cg.red));
+    if (tid == 0) {
+        const double rr_ = (double)ab[0].hi + (double)ab[0].lo;
+        const double rq_ = (double)ab[1].hi + (double)ab[1].lo;
+        cs.beta = act == 2 ? 0.f : (float)(-rq_ / cs.pq);   // gamma of the carried direction
+        cs.rr = rr_;
+        cs.rmax = sqrt(rr_);
+        cs.S = rnorm;
+    }
+    __syncthreads();
+    const float gamma = cs.beta;
+    for (int k = tid; k < npe; k += nt) {
+        const int off = poff[k];
+        pf[off] = rf[off] + gamma * pf[off];
+    }
+    __syncthreads();
+    return false;
+}
+
 template <int FDN>
 __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, int &refine, int &status, double &rnorm)
 {
     const SetDev &S = *cg.S;
     const SmemCell &sm = *cg.sm;
-    double *__restrict__ vbox = cg.vbox;
-    const double *__restrict__ rho = cg.rho;
-    double *__restrict__ r64 = cg.r64;
+    const float *__restrict__ r32 = reinterpret_cast<const float *>(cg.r64);   // last true residual, FP32
     float *__restrict__ pf = cg.pf;
     float *__restrict__ rf = cg.rf;
     float *__restrict__ qf = cg.qf;
@@ -808,10 +977,10 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
     {
         double a0[1];
         DF a = {0.f, 0.f};
-        const double sc = 1.0 / cg.r0n;
+        const F32Scale sc = f32_scale(1.0 / cg.r0n);
         for (int k = tid; k < npe; k += nt) {
             const int off = poff[k];
-            const float r = (float)(r64[k] * sc);
+            const float r = sc.apply(r32[k]);
             rf[off] = r;
             ef[off] = 0.f;
             pf[off] = r;
@@ -822,11 +991,7 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
         rr = a0[0];
     }
     // scalars of the iteration, kept by thread 0 and broadcast through shared memory
-    __shared__ struct {
-        double rr, rmax, S, pq;
-        float alpha, beta;
-        int act;   // 0 continue, 1 FP64 replacement, 2 replacement after a breakdown
-    } cs;
+    __shared__ SweepScalars cs;
     if (tid == 0) {
         cs.rr = rr;
         cs.rmax = sqrt(rr);
@@ -886,41 +1051,8 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
         pending = false;
         ++iters;
         if (act) {
-            const double S_ = cs.S;
-            for (int k = tid; k < npe; k += nt) {
-                const int off = poff[k];
-                vbox[off] += ((double)ef[off] + (double)alpha * (double)pf[off]) * S_;
-                ef[off] = 0.f;
-            }
-            __syncthreads();
-            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, cg.fdn, sm.center64, red));
             ++refine;
-            if (rnorm <= stop) break;
-            const double sc = 1.0 / rnorm;
-            DF ab[2] = {{0.f, 0.f}, {0.f, 0.f}};
-            for (int k = tid; k < npe; k += nt) {
-                const int off = poff[k];
-                const float r = (float)(r64[k] * sc);
-                rf[off] = r;
-                df_fma(ab[0], r, r);
-                df_fma(ab[1], r, qf[off]);
-            }
-            block_sum_df<2>(ab, red2);
-            if (tid == 0) {
-                const double rr_ = (double)ab[0].hi + (double)ab[0].lo;
-                const double rq_ = (double)ab[1].hi + (double)ab[1].lo;
-                cs.beta = act == 2 ? 0.f : (float)(-rq_ / cs.pq);   // gamma of the carried direction
-                cs.rr = rr_;
-                cs.rmax = sqrt(rr_);
-                cs.S = rnorm;
-            }
-            __syncthreads();
-            const float gamma = cs.beta;
-            for (int k = tid; k < npe; k += nt) {
-                const int off = poff[k];
-                pf[off] = rf[off] + gamma * pf[off];
-            }
-            __syncthreads();
+            if (sweep_replace(cg, cs, alpha, act, rnorm)) break;
             continue;
         }
         alpha_p = alpha;
@@ -1022,8 +1154,8 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
 // outer sums, then v at every PE point with r^l Y_lm from the Cartesian
 // recurrences of solid_harmonics in FP32.  Points are visited in radius order,
 // so the lanes of a warp share one or two bins and read the same moments.
-__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, double *__restrict__ vbox,
-                                             float *__restrict__ gs)
+__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, double *vbox, float *__restrict__ gs,
+                                             bool df)
 {
     __shared__ float cn[kNlm];   // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0)
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -1100,7 +1232,8 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
                 }
             }
         }
-        vbox[S.pe_off[kk]] = (double)v;
+        if (df) reinterpret_cast<float2 *>(vbox)[S.pe_off[kk]] = make_float2(v, 0.f);   // double-float pair
+        else vbox[S.pe_off[kk]] = (double)v;
     }
 }
 
@@ -1144,12 +1277,14 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 const int d = tid / 8, s = tid % 8;
                 sm.cw64[d][s] = sm.C.cw64[d][s];
                 sm.cw32[d][s] = sm.C.cw32[d][s];
+                sm.cwdf[d][s] = dw_split(sm.C.cw64[d][s]);
             }
             if (tid == 0) {
                 double c = 0.0;
                 for (int d = 0; d < sm.C.ndir; ++d) c += sm.C.cw64[d][0];
                 sm.center64 = c;
                 sm.center32 = (float)c;
+                sm.centerdf = dw_split(c);
                 s_cell = pr.cell;
             }
             __syncthreads();
@@ -1160,6 +1295,18 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         if (tid < 6) sm.ds[tid] = S.dstride[tid];
         if (tid == 0) s_flag = 0;
         const int ndir = C.ndir, fdn = C.fd_n;
+        // mixed pairs on the one-sweep CG hold v as double-float pairs in vbox while
+        // they solve (converted to FP64 afterwards) and take every residual in
+        // double-float arithmetic; the others keep FP64 throughout
+        const bool dfm = mixed && fdn <= 4 &&
+                         (S.n_groups + kSweepChunkGroups * nt - 1) / (kSweepChunkGroups * nt) <= kMaxSweepChunks;
+        float2 *vb = reinterpret_cast<float2 *>(vbox);
+        float2 *b2 = reinterpret_cast<float2 *>(slot + W.off_b2);
+        float *r32 = reinterpret_cast<float *>(r64);
+        auto residual = [&]() -> double {
+            return dfm ? residual_df_n(fdn, S, vb, b2, r32, sm.cwdf, sm.centerdf, sm.ds, ndir, red)
+                       : residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red);
+        };
 
         // ---- Step III: pair density on PE, g = MOD(g_ij + m, N) (Eq. l2g) ----
         for (int k = tid; k < S.n_pe; k += nt) {
@@ -1167,7 +1314,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             unpack_m(S.pe_m[k], m0, m1, m2);
             const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
                       g2 = wrapi(pr.g[2] + m2, C.n[2]);
-            rho[k] = phi_at(C, pr.i, g0, g1, g2) * phi_at(C, pr.j, g0, g1, g2);
+            const double rk = phi_at(C, pr.i, g0, g1, g2) * phi_at(C, pr.j, g0, g1, g2);
+            rho[k] = rk;
+            if (dfm) b2[k] = dw_split(kFourPi * rk);
         }
         __syncthreads();
 
@@ -1237,13 +1386,14 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             } else {
                 for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * S.T64[(size_t)lm * S.n_shell + h];
             }
-            vbox[S.halo_off[h]] = v;
+            if (dfm) vb[S.halo_off[h]] = make_float2((float)v, 0.f);
+            else vbox[S.halo_off[h]] = v;
         }
         __syncthreads();
 
         // ---- Step IV: Poisson solve (Eq. pe) ----
         // b = 4 pi rho + (Dirichlet terms): the residual of v = 0 on PE
-        double rr2 = residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red);
+        double rr2 = residual();
         const double bn = sqrt(rr2);
         const double stop = C.tol * bn;
         int iters = 0, refine = 1, status = 0;
@@ -1278,10 +1428,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                     const int kk = inv[((size_t)u0 * S.B[1] + u1) * S.B[2] + u2];
                     if (kk >= 0) v = (double)src[kk];
                 }
-                vbox[S.pe_off[k]] = v;
+                if (dfm) vb[S.pe_off[k]] = make_float2((float)v, 0.f);
+                else vbox[S.pe_off[k]] = v;
             }
             __syncthreads();
-            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            rnorm = sqrt(residual());
             rr2 = rnorm * rnorm;
             ++refine;
             // a previous solution that the pair has moved away from starts worse than
@@ -1293,9 +1444,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 bin_moments(S, C, rho, gs, qpart);
                 __syncthreads();
             }
-            multipole_guess(S, C, vbox, gs);
+            multipole_guess(S, C, vbox, gs, dfm);
             __syncthreads();
-            rnorm = sqrt(residual_pass(S, vbox, rho, r64, sm.cw64, sm.ds, ndir, fdn, sm.center64, red));
+            rnorm = sqrt(residual());
             rr2 = rnorm * rnorm;
             ++refine;
         }
@@ -1367,14 +1518,26 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             cg.bn = bn;
             cg.r0n = rnorm;
             cg.inner_red = inner_red;
-            if ((S.n_groups + kSweepChunkGroups * nt - 1) / (kSweepChunkGroups * nt) <= kMaxSweepChunks) {
+            cg.b2 = b2;
+            if (dfm) {
                 switch (fdn) {
                 case 1: cg_mixed_sweep<1>(cg, iters, refine, status, rnorm); break;
                 case 2: cg_mixed_sweep<2>(cg, iters, refine, status, rnorm); break;
                 case 3: cg_mixed_sweep<3>(cg, iters, refine, status, rnorm); break;
-                case 4: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
-                default: cg_mixed(cg, iters, refine, status, rnorm); break;
+                default: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
                 }
+                // v back to FP64 on PE and on the halo (far field, low words zero)
+                __syncthreads();
+                for (int k = tid; k < S.n_pe; k += nt) {
+                    const int off = S.pe_off[k];
+                    const float2 t = vb[off];
+                    vbox[off] = (double)t.x + (double)t.y;
+                }
+                for (int h = tid; h < S.n_halo; h += nt) {
+                    const int off = S.halo_off[h];
+                    vbox[off] = (double)vb[off].x;
+                }
+                __syncthreads();
             } else {
                 cg_mixed(cg, iters, refine, status, rnorm);
             }
@@ -2344,6 +2507,7 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
     W.off_q = slots.off_q;
     W.off_e = slots.off_e;
     W.off_gs = slots.off_gs;
+    W.off_b2 = slots.off_b2;
     if (mixed) k_pair_solve<float><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     else k_pair_solve<double><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     return cudaGetLastError();
