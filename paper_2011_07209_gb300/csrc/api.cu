@@ -78,7 +78,7 @@ struct exx_ctx {
     CellDev *h_cells = nullptr;       // pinned
     CellResult *h_res = nullptr;      // pinned
     int cells_cap = 0;
-    int inner_shift = 10;
+    int inner_shift = 14;             // reliable update when the FP32 residual fell by 2^-14 (EXX_INNER_SHIFT)
     int solver = EXX_SOLVER_CTA;   // exx_ctx_set_solver
     int cluster_cap = -1;     // dynamic shared memory a cluster CTA can take (bytes), -1 unknown
     int last_path = 0;        // 0: per-CTA solver, 1: cluster solver (of the last solve)

@@ -34,7 +34,11 @@ __device__ __forceinline__ void unpack_m(int32_t p, int &m0, int &m1, int &m2)
 
 __device__ __forceinline__ int wrapi(int a, int n)
 {
-    int r = a % n;
+    // within one period of [0, n) (grid offsets inside the cell) without a division
+    if (a >= n) a -= n;
+    else if (a < 0) a += n;
+    if ((unsigned)a < (unsigned)n) return a;
+    const int r = a % n;
     return r < 0 ? r + n : r;
 }
 
@@ -544,6 +548,9 @@ struct SmemCell {
     float cw32[6][8];
     float2 cwdf[6][8];   // cw64 as double-float pairs
     float2 centerdf;
+    float cn[kNlm];      // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0): solid_sum32
+    float hf[3][3];      // h[a][b] / N_b: Cartesian position of a grid offset, FP32
+    float Qc[kNlm];      // 4 pi / (2l+1) Q_lm of the current pair, FP32
     double Q[kNlm];
     float Qf[kNlm];
     double center64;
@@ -1077,6 +1084,65 @@ __device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 
     return ri * ((l & 1) ? r2 : 1.f) * ((l & 2) ? r4 : 1.f) * ((l & 4) ? r8 : 1.f);
 }
 
+// sum over lm (l <= lmax) of S_lm(x, y, z) coef(lm, l), with r^l Y_lm from the
+// Cartesian recurrences of solid_harmonics evaluated in FP32 (about 1e-6 of
+// the largest term, against 6e-8 for the rounded FP64 tables); cn holds N_l0
+// at l^2 + l and sqrt2 N_lm at l^2 + l + m.
+template <class Coef>
+__device__ __forceinline__ float solid_sum32(float x, float y, float z, int lmax, const float *cn, const Coef &coef)
+{
+    const float r2 = x * x + y * y + z * z;
+    float v = 0.f;
+    float Am = 1.f, Bm = 0.f, dfact = 1.f;   // (x + iy)^m, (2m-1)!!
+#pragma unroll
+    for (int m = 0; m <= 6; ++m) {
+        if (m > 0) {
+            const float An = x * Am - y * Bm;
+            Bm = x * Bm + y * Am;
+            Am = An;
+            dfact *= (float)(2 * m - 1);
+        }
+        float q1 = 0.f, q2 = 0.f;   // Q_{l-1}^m, Q_{l-2}^m
+#pragma unroll
+        for (int l = m; l <= 6; ++l) {
+            float q;
+            if (l == m) q = dfact;
+            else if (l == m + 1) q = (float)(2 * m + 1) * z * dfact;
+            else q = ((float)(2 * l - 1) * z * q1 - (float)(l + m - 1) * r2 * q2) * (1.f / (float)(l - m));
+            q2 = q1;
+            q1 = q;
+            if (l <= lmax) {
+                const int i0 = l * l + l;
+                const float c = cn[i0 + m] * q;
+                if (m == 0) v += c * coef(i0, l);
+                else v += c * (Am * coef(i0 + m, l) + Bm * coef(i0 - m, l));
+            }
+        }
+    }
+    return v;
+}
+
+// r^-(2l+1), l = 0..6, from 1/r
+struct RinvPows {
+    float f[7];
+    __device__ explicit RinvPows(float ri)
+    {
+        const float ri2 = ri * ri;
+        f[0] = ri;
+#pragma unroll
+        for (int l = 1; l < 7; ++l) f[l] = f[l - 1] * ri2;
+    }
+};
+
+__device__ __forceinline__ void xyz_of(const float (*h)[3], int32_t pm, float &x, float &y, float &z)
+{
+    int m0, m1, m2;
+    unpack_m(pm, m0, m1, m2);
+    x = h[0][0] * m0 + h[0][1] * m1 + h[0][2] * m2;
+    y = h[1][0] * m0 + h[1][1] * m1 + h[1][2] * m2;
+    z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
+}
+
 __device__ __forceinline__ void pe_xyz(const SetDev &S, const float (*h)[3], int k, float &x, float &y, float &z)
 {
     int m0, m1, m2;
@@ -1154,10 +1220,9 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
 // outer sums, then v at every PE point with r^l Y_lm from the Cartesian
 // recurrences of solid_harmonics in FP32.  Points are visited in radius order,
 // so the lanes of a warp share one or two bins and read the same moments.
-__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, double *vbox, float *__restrict__ gs,
-                                             bool df)
+__device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, const float *cn,
+                                             const float (*hf)[3], double *vbox, float *__restrict__ gs, bool df)
 {
-    __shared__ float cn[kNlm];   // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0)
     const int tid = threadIdx.x, nt = blockDim.x;
     float *A = gs, *B = gs + kGuessBins * kNlm;
     // inner sums from below, outer sums from above, half of the own bin each
@@ -1177,61 +1242,19 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
                 acc += a;
             }
         }
-    } else if (tid < 3 * kNlm) {
-        const int lm = tid - 2 * kNlm;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= lm) ++l;
-        const int m = lm - l * l - l;
-        float c = 0.f;
-        if (m >= 0) {
-            double ratio = 1.0;   // (l-m)!/(l+m)!
-            for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
-            const double nlm = sqrt((2.0 * l + 1.0) / kFourPi * ratio);
-            c = (float)(m == 0 ? nlm : 1.4142135623730951 * nlm);
-        }
-        cn[lm] = c;
     }
     __syncthreads();
-    float h[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
     const int lmax = C.lmax;
     for (int j = tid; j < S.n_pe; j += nt) {
         const int kk = S.gs_perm[j];
         const float *Ab = A + (int)S.gs_bin[kk] * kNlm, *Bb = B + (int)S.gs_bin[kk] * kNlm;
         float x, y, z;
-        pe_xyz(S, h, kk, x, y, z);
+        xyz_of(hf, S.pe_m[kk], x, y, z);
         const float r2 = x * x + y * y + z * z;
-        const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f, ri2 = ri * ri;
-        float v = 0.f;
-        float Am = 1.f, Bm = 0.f, dfact = 1.f, fm = ri;   // (x + iy)^m, (2m-1)!!, r^-(2m+1)
-#pragma unroll
-        for (int m = 0; m <= 6; ++m) {
-            if (m > 0) {
-                const float An = x * Am - y * Bm;
-                Bm = x * Bm + y * Am;
-                Am = An;
-                dfact *= (float)(2 * m - 1);
-                fm *= ri2;
-            }
-            float q1 = 0.f, q2 = 0.f, fl = fm;   // Q_{l-1}^m, Q_{l-2}^m, r^-(2l+1)
-#pragma unroll
-            for (int l = m; l <= 6; ++l) {
-                float q;
-                if (l == m) q = dfact;
-                else if (l == m + 1) q = (float)(2 * m + 1) * z * dfact;
-                else q = ((float)(2 * l - 1) * z * q1 - (float)(l + m - 1) * r2 * q2) * (1.f / (float)(l - m));
-                q2 = q1;
-                q1 = q;
-                if (l > m) fl *= ri2;
-                if (l <= lmax) {
-                    const int i0 = l * l + l;
-                    const float c = (12.566370614359172f / (float)(2 * l + 1)) * cn[i0 + m] * q;
-                    if (m == 0) v += c * (fl * Ab[i0] + Bb[i0]);
-                    else v += c * (Am * (fl * Ab[i0 + m] + Bb[i0 + m]) + Bm * (fl * Ab[i0 - m] + Bb[i0 - m]));
-                }
-            }
-        }
+        const RinvPows rp(r2 > 0.f ? rsqrtf(r2) : 0.f);
+        const float v = solid_sum32(x, y, z, lmax, cn, [&](int i, int l) {
+            return (12.566370614359172f / (float)(2 * l + 1)) * (rp.f[l] * Ab[i] + Bb[i]);
+        });
         if (df) reinterpret_cast<float2 *>(vbox)[S.pe_off[kk]] = make_float2(v, 0.f);   // double-float pair
         else vbox[S.pe_off[kk]] = (double)v;
     }
@@ -1278,6 +1301,22 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 sm.cw64[d][s] = sm.C.cw64[d][s];
                 sm.cw32[d][s] = sm.C.cw32[d][s];
                 sm.cwdf[d][s] = dw_split(sm.C.cw64[d][s]);
+            } else if (tid >= 64 && tid < 64 + kNlm) {
+                const int lm = tid - 64;
+                int l = 0;
+                while ((l + 1) * (l + 1) <= lm) ++l;
+                const int m = lm - l * l - l;
+                float c = 0.f;
+                if (m >= 0) {
+                    double ratio = 1.0;   // (l-m)!/(l+m)!
+                    for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+                    const double nlm = sqrt((2.0 * l + 1.0) / kFourPi * ratio);
+                    c = (float)(m == 0 ? nlm : 1.4142135623730951 * nlm);
+                }
+                sm.cn[lm] = c;
+            } else if (tid >= 128 && tid < 137) {
+                const int a = (tid - 128) / 3, b = (tid - 128) % 3;
+                sm.hf[a][b] = (float)(sm.C.h[a][b] / sm.C.n[b]);
             }
             if (tid == 0) {
                 double c = 0.0;
@@ -1372,6 +1411,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 const double q = (tid < (C.lmax + 1) * (C.lmax + 1)) ? s * C.dv : 0.0;
                 sm.Q[tid] = q;
                 sm.Qf[tid] = (float)q;
+                int l = 0;
+                while ((l + 1) * (l + 1) <= tid) ++l;
+                sm.Qc[tid] = (float)(kFourPi / (2 * l + 1) * q);
             }
             __syncthreads();
         }
@@ -1444,7 +1486,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 bin_moments(S, C, rho, gs, qpart);
                 __syncthreads();
             }
-            multipole_guess(S, C, vbox, gs, dfm);
+            multipole_guess(S, C, sm.cn, sm.hf, vbox, gs, dfm);
             __syncthreads();
             rnorm = sqrt(residual());
             rr2 = rnorm * rnorm;
@@ -1600,9 +1642,11 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                     const int s = k - S.n_pe;
                     unpack_m(S.sh_m[s], m0, m1, m2);
                     if (mixed) {
-                        float vf = 0.f;
-                        for (int lm = 0; lm < kNlm; ++lm) vf += sm.Qf[lm] * S.T32[(size_t)lm * S.n_shell + s];
-                        v = vf;
+                        // Eq. me evaluated in FP32 from the Cartesian recurrences
+                        float x, y, z;
+                        xyz_of(sm.hf, S.sh_m[s], x, y, z);
+                        const RinvPows rp(rsqrtf(x * x + y * y + z * z));
+                        v = solid_sum32(x, y, z, C.lmax, sm.cn, [&](int i, int l) { return rp.f[l] * sm.Qc[i]; });
                     } else {
                         v = 0.0;
                         for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * S.T64[(size_t)lm * S.n_shell + s];
