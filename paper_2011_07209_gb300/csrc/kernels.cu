@@ -521,6 +521,52 @@ __device__ __forceinline__ double residual_df_n(int fdn, const SetDev &S, const 
     }
 }
 
+// Step V integrals of one pair from the double-float solution (v as hi/lo
+// pairs in the box, 4 pi rho as pairs): sum rho v and sum m_alpha rho d_b v,
+// d_b v the central first difference along lattice axis b (weights w1).  Every
+// product and sum in double-float; in thread 0, out[0] = sum rho v and
+// out[1 + 3 b + alpha] = sum m_alpha rho d_b v (no dV).
+__device__ __noinline__ void energy_stress_df(const SetDev &S, const float2 (*w1)[8], const float2 *vb,
+                                              const float2 *__restrict__ b2, bool want_sigma, int fdn, float2 *red2,
+                                              double *out)
+{
+    DF acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = {0.f, 0.f};
+    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        const float2 b = b2[k];
+        const float2 e = dw_mul(b, vb[off]);
+        acc[0] = df_sum(acc[0], {e.x, e.y});
+        if (!want_sigma) continue;
+        int m0, m1, m2;
+        unpack_m(S.pe_m[k], m0, m1, m2);
+        const float mf[3] = {(float)m0, (float)m1, (float)m2};
+#pragma unroll
+        for (int db = 0; db < 3; ++db) {
+            const int st = S.gstride[db];
+            float2 d = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int s_ = 1; s_ <= 4; ++s_) {
+                if (s_ <= fdn) {
+                    const float2 vm = vb[off - s_ * st];
+                    d = dw_add(d, dw_mul(w1[db][s_], dw_add(vb[off + s_ * st], make_float2(-vm.x, -vm.y))));
+                }
+            }
+            const float2 rd = dw_mul(b, d);   // 4 pi rho d_b v
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                const float2 p = two_prod(mf[al], rd.x);   // m_alpha is an integer below 2^10: exact
+                acc[1 + 3 * db + al] = df_sum(acc[1 + 3 * db + al], {p.x, __fmaf_rn(mf[al], rd.y, p.y)});
+            }
+        }
+    }
+    block_sum_df<10>(acc, red2);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 10; ++k) out[k] = ((double)acc[k].hi + (double)acc[k].lo) / kFourPi;
+}
+
 // x * sc in FP32 for any FP64 scale sc (sc = m 2^e, x m rounded once, then an
 // exact power-of-two scaling), so that tiny residuals reach the O(1) frame.
 struct F32Scale {
@@ -551,6 +597,7 @@ struct SmemCell {
     float cn[kNlm];      // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0): solid_sum32
     float hf[3][3];      // h[a][b] / N_b: Cartesian position of a grid offset, FP32
     float Qc[kNlm];      // 4 pi / (2l+1) Q_lm of the current pair, FP32
+    float2 w1df[3][8];   // first-derivative weights w1dx as double-float pairs
     double Q[kNlm];
     float Qf[kNlm];
     double center64;
@@ -1317,6 +1364,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             } else if (tid >= 128 && tid < 137) {
                 const int a = (tid - 128) / 3, b = (tid - 128) % 3;
                 sm.hf[a][b] = (float)(sm.C.h[a][b] / sm.C.n[b]);
+            } else if (tid >= 160 && tid < 184) {
+                const int a = (tid - 160) / 8, b = (tid - 160) % 8;
+                sm.w1df[a][b] = dw_split(sm.C.w1dx[a][b]);
             }
             if (tid == 0) {
                 double c = 0.0;
@@ -1492,6 +1542,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             rr2 = rnorm * rnorm;
             ++refine;
         }
+        double es[10];   // Step V sums of the double-float path (valid in thread 0)
         if (!mixed) {
             // plain FP64 CG: x in vbox (PE), r in r64, p in pbox, q in qv
             double *pd = (double *)pbox;
@@ -1568,16 +1619,14 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 case 3: cg_mixed_sweep<3>(cg, iters, refine, status, rnorm); break;
                 default: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
                 }
-                // v back to FP64 on PE and on the halo (far field, low words zero)
                 __syncthreads();
+                // Step V integrals from the double-float solution
+                energy_stress_df(S, sm.w1df, vb, b2, C.stress_mode != 2, fdn, reinterpret_cast<float2 *>(red), es);
+                // v back to FP64 on PE for D and the warm-start store
                 for (int k = tid; k < S.n_pe; k += nt) {
                     const int off = S.pe_off[k];
                     const float2 t = vb[off];
                     vbox[off] = (double)t.x + (double)t.y;
-                }
-                for (int h = tid; h < S.n_halo; h += nt) {
-                    const int off = S.halo_off[h];
-                    vbox[off] = (double)vb[off].x;
                 }
                 __syncthreads();
             } else {
@@ -1597,9 +1646,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         // ---- Step V: energy and stress integrals (Eqs. exxGen_mlwf, sxx_working, d1_1) ----
         double acc[10];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+        for (int k = 0; k < 10; ++k) acc[k] = dfm ? es[k] : 0.0;
         const bool want_sigma = C.stress_mode != 2;
-        for (int k = tid; k < S.n_pe; k += nt) {
+        for (int k = tid; k < (dfm ? 0 : S.n_pe); k += nt) {
             const int off = S.pe_off[k];
             const double rk = rho[k];
             const double v = vbox[off];
@@ -1627,7 +1676,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 for (int al = 0; al < 3; ++al) acc[1 + 3 * b + al] += mb[al] * rd;
             }
         }
-        block_sum<10>(acc, red);
+        if (!dfm) block_sum<10>(acc, red);
 
         // ---- D^i += v phi_j, D^j += v phi_i on PE and shell (Eq. Dxx, Step V) ----
         if (C.dxx) {
