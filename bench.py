@@ -147,9 +147,11 @@ def reduce_over_ranks(elapsed_ms: float, n_pairs: int, dist, device):
 def algorithmic_bytes(n_pairs, total_iter, total_refine, n_pe, n_me, s):
     """Bytes the pair solver must move per launch:
     CG: 7 N_PE s per iteration (x, r, p read + written, p read by the stencil);
-    refinement: 3 N_PE 8 per FP64 residual (v, rho read, r written);
+    true residual: FP64 path 24 N_PE (v, rho read, r written in FP64), mixed
+    path 20 N_PE (v and 4 pi rho read as double-float pairs, r written in FP32);
     per pair: gather 2 N_ME 8, D read-modify-write 2 N_ME 16, rho 8 N_PE."""
-    return (total_iter * 7.0 * n_pe * s + total_refine * 3.0 * n_pe * 8.0
+    per_residual = 20.0 if s == 4 else 24.0
+    return (total_iter * 7.0 * n_pe * s + total_refine * per_residual * n_pe
             + n_pairs * (2.0 * n_me * 8.0 + 2.0 * n_me * 16.0 + 8.0 * n_pe))
 
 

@@ -105,8 +105,13 @@ typedef struct {
     int cg_max_iter;        /* cap on CG iterations per pair (summed over refinements) */
     int nq;                 /* NK candidate count N_q of Algorithm 1 (paper default 15) */
     int precision;          /* EXX_FP64: every step in FP64.  EXX_MIXED: FP32 stencil and */
-                            /* axpy inside an FP64-residual refinement loop; dot products */
-                            /* exact-product double-float; moments, E, sigma, D in FP64   */
+                            /* axpy inside a true-residual refinement loop; dot products  */
+                            /* exact-product double-float; moments and far field from     */
+                            /* FP32 tables with FP64 sums; the true residuals, the        */
+                            /* solution update and E, sigma in double-float (FP32 hi/lo   */
+                            /* pairs, about 48 bits) on the CTA solver, FP64 on the       */
+                            /* cluster solver and for fd_order > 4; D in FP64 from an     */
+                            /* FP32 far field on the shell                                */
     int frozen;             /* 1: subdomain offsets and NK aux directions stay those of the */
                             /* plan's cell while h changes (fixed number of points,         */
                             /* Sec. III B 2); 0: rebuilt whenever the cell changes          */
@@ -159,9 +164,9 @@ typedef struct {
     int n_stcl;             /* stencil points 2 n (3 + n_aux) + 1 */
     int max_cg_iter;        /* largest per-pair CG iteration count */
     long long total_cg_iter;/* CG iterations summed over pairs */
-    int max_refine;         /* largest number of FP64 residual evaluations of a pair */
+    int max_refine;         /* largest number of true-residual evaluations of a pair */
     int failed_pair;        /* index of the first failed pair, or -1 */
-    long long total_refine; /* FP64 residual evaluations summed over pairs */
+    long long total_refine; /* true-residual evaluations summed over pairs */
     double p_int;           /* EXX contribution to the internal pressure, Tr Pi_xx^pot / 3,  */
                             /* Ha/bohr^3 (Eq. pxx_working; Eq. liq_press in EXX_STRESS_CUBIC) */
     int n_warm;             /* pairs that started from a previous solution (warm_start)      */

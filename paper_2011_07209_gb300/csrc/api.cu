@@ -511,7 +511,7 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
     s.off_e = o + 128;
     o += vecb;
     s.off_gs = o + 128;
-    o += align256(2 * kGuessBins * kNlm * 4 + 256);
+    o += align256(6 * kGuessBins * kNlm * 4 + 256);
     s.off_b2 = o + 128;
     o += align256(8 * npe_max + 256);
     s.slot_bytes = o;

@@ -1122,7 +1122,8 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
 // with |r'| < r decided by radial bin (half of the point's own bin on each side).
 // Outside PE this is the far field of Eq. me, which is why it is close to the
 // solution of Eq. pe; it only sets where CG starts, not what it converges to.
-// gs: [2][kGuessBins][kNlm] scratch of the CTA (inner, outer moments per bin).
+// gs: scratch of the CTA, [2][2 kGuessBins][kNlm] moments per half bin, then
+// [2][kGuessBins][kNlm] cumulative inner and outer moments per bin.
 constexpr double kWarmAccept = 0.05;   // warm starts kept when |b - A v_prev| <= 5 % of |b|
 
 __device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 7, without branches
@@ -1199,13 +1200,17 @@ __device__ __forceinline__ void pe_xyz(const SetDev &S, const float (*h)[3], int
     z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
 }
 
-// Multipole moments of rho per radial bin, one warp per bin over the
-// radius-sorted copy of the solid-harmonic table (no atomics: the same sums on
-// every run): gs gets the inner moments rho r^l Y_lm dV and the outer moments
-// rho r^-(l+1) Y_lm dV of each bin, and qpart[w] the FP64 sum of the inner
-// moments over warp w's bins.  The sum over the bins is the moment Q_lm of
+// Multipole moments of rho per radial bin over the radius-sorted copy of the
+// solid-harmonic table (no atomics: the same sums on every run).  Each bin is
+// split into two halves of its sorted range; the 2 kGuessBins pieces, in order
+// of decreasing radius, are dealt to the warps in snake order so that warps
+// get similar numbers of points (bin sizes grow as the square of the radius).
+// gs receives per piece the inner moments rho r^l Y_lm dV and the outer
+// moments rho r^-(l+1) Y_lm dV (FP32), and qpart[w] the FP64 sum of the inner
+// moments of warp w's pieces; their sum over the warps is the moment Q_lm of
 // Eq. mepole (up to dV), accumulated like the one-pass moments: FP32 over 32
 // points, FP64 beyond.
+constexpr int kGuessPieces = 2 * kGuessBins;
 __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, const double *__restrict__ rho,
                                          float *__restrict__ gs, double (*qpart)[kNlm])
 {
@@ -1217,13 +1222,15 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
     float h[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
-    float *A = gs, *B = gs + kGuessBins * kNlm;
+    float *PA = gs, *PB = gs + kGuessPieces * kNlm;   // per piece j: bin kGuessBins - 1 - j / 2, half j % 2
     const double dv = C.dv;
     double w0 = 0.0, w1 = 0.0;
-    // warp w takes bins w and kGuessBins - 1 - w, a small and a large one
-    for (int u = warp; u < kGuessBins; u += nwarps) {
-        const int b = u < nwarps ? u : kGuessBins - 1 - (u - nwarps);
-        const int k0 = S.gs_bstart[b], k1 = S.gs_bstart[b + 1];
+    for (int base = 0; base < kGuessPieces; base += nwarps) {   // each round a permutation of base + [0, nwarps)
+        const int j = base + (((base / nwarps) & 1) ? nwarps - 1 - warp : warp);
+        if (j >= kGuessPieces) continue;
+        const int b = kGuessBins - 1 - j / 2;
+        const int b0_ = S.gs_bstart[b], b1_ = S.gs_bstart[b + 1], mid = b0_ + (b1_ - b0_) / 2;
+        const int k0 = (j & 1) ? mid : b0_, k1 = (j & 1) ? b1_ : mid;
         double a0 = 0.0, a1 = 0.0;
         float b0 = 0.f, b1 = 0.f;
         for (int x = k0; x < k1; x += 32) {
@@ -1250,11 +1257,11 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
             a0 += f0;
             a1 += f1;
         }
-        A[b * kNlm + lane] = (float)(a0 * dv);
-        B[b * kNlm + lane] = (float)(b0 * dv);
+        PA[j * kNlm + lane] = (float)(a0 * dv);
+        PB[j * kNlm + lane] = (float)(b0 * dv);
         if (has1) {
-            A[b * kNlm + lane + 32] = (float)(a1 * dv);
-            B[b * kNlm + lane + 32] = (float)(b1 * dv);
+            PA[j * kNlm + lane + 32] = (float)(a1 * dv);
+            PB[j * kNlm + lane + 32] = (float)(b1 * dv);
         }
         w0 += a0;
         w1 += a1;
@@ -1271,23 +1278,21 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
                                              const float (*hf)[3], double *vbox, float *__restrict__ gs, bool df)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    float *A = gs, *B = gs + kGuessBins * kNlm;
-    // inner sums from below, outer sums from above, half of the own bin each
+    const float *PA = gs, *PB = gs + kGuessPieces * kNlm;   // per piece (bin_moments)
+    float *A = gs + 2 * kGuessPieces * kNlm, *B = A + kGuessBins * kNlm;
+    // bin moments (both halves), then inner sums from below and outer sums from
+    // above, half of the own bin each
     if (tid < 2 * kNlm) {
         const int lm = tid % kNlm;
+        const float *P = tid < kNlm ? PA : PB;
+        float *Q = tid < kNlm ? A : B;
         float acc = 0.f;
-        if (tid < kNlm) {
-            for (int b = 0; b < kGuessBins; ++b) {
-                const float a = A[b * kNlm + lm];
-                A[b * kNlm + lm] = acc + 0.5f * a;
-                acc += a;
-            }
-        } else {
-            for (int b = kGuessBins - 1; b >= 0; --b) {
-                const float a = B[b * kNlm + lm];
-                B[b * kNlm + lm] = acc + 0.5f * a;
-                acc += a;
-            }
+        for (int i = 0; i < kGuessBins; ++i) {
+            const int b = tid < kNlm ? i : kGuessBins - 1 - i;
+            const int jp = 2 * (kGuessBins - 1 - b);
+            const float a = P[jp * kNlm + lm] + P[(jp + 1) * kNlm + lm];
+            Q[b * kNlm + lm] = acc + 0.5f * a;
+            acc += a;
         }
     }
     __syncthreads();

@@ -21,7 +21,7 @@ struct SolveSlots {
     char *base;
     size_t slot_bytes;
     size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e;
-    size_t off_gs;   // 2 kGuessBins kNlm floats: binned moments of the starting guess
+    size_t off_gs;   // 6 kGuessBins kNlm floats: binned moments of the starting guess
     size_t off_b2;   // n_pe float pairs: 4 pi rho as hi + lo (double-float residuals)
     int n_slots;
 };
