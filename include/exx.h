@@ -252,6 +252,20 @@ int exx_pair_list_noalloc(const exx_cell *cell, const double *centres, int n_orb
  * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);
 
+/* Strain of a cell relative to a reference cell (both lattice[alpha][a], rows
+ * are lattice vectors, 9 doubles each; caller-owned host memory), the
+ * criterion for re-assembling frozen proto-subdomains: with subdomains of a
+ * fixed number of points that deform with the cell (Sec. III B 2), strong
+ * anisotropic strain calls for re-assembling quasi-spherical ones from scratch,
+ * by a strain criterion or a step stride (done by creating a new plan whose
+ * reference cell is the current one).  F = h h0^-1 with h = lattice^T,
+ * E = (F^T F - I) / 2 (Green-Lagrange strain, invariant under rotations of
+ * the cell).  out[0] = the largest |eigenvalue| of E, out[1] = det F - 1 (the
+ * relative volume change).  Host arithmetic only: needs no GPU.  Errors:
+ * EXX_ERR_ARG for a null pointer, EXX_ERR_CELL for a cell that is singular or
+ * not right-handed. */
+int exx_cell_strain(const double *lattice0, const double *lattice, double out[2]);
+
 /* Choose the persistent pair solver of the mixed-precision path (Step IV).
  * EXX_SOLVER_CTA (default): one CTA of 1024 threads per pair, CG vectors in
  * HBM as dense boxes.  EXX_SOLVER_CLUSTER: one thread-block cluster of 16 CTAs

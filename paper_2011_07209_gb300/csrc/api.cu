@@ -730,6 +730,18 @@ int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int hw[3]
     return EXX_OK;
 }
 
+int exx_cell_strain(const double *lattice0, const double *lattice, double out[2])
+{
+    if (!lattice0 || !lattice || !out) return EXX_ERR_ARG;
+    double l0[3][3], l1[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            l0[a][b] = lattice0[3 * a + b];
+            l1[a][b] = lattice[3 * a + b];
+        }
+    return cell_strain(l0, l1, out[0], out[1]);
+}
+
 int exx_get_pair_list(exx_plan *p, int cap, int *n, int *rows)
 {
     if (!p || !n) return EXX_ERR_ARG;

@@ -53,6 +53,55 @@ int make_metric(const double lattice[3][3], const int n[3], Metric &m)
     return EXX_OK;
 }
 
+// Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations (each
+// rotation zeroes one off-diagonal element; a few sweeps reach rounding level).
+static void sym3_eigenvalues(double a[3][3], double ev[3])
+{
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double diag = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-30 * diag || off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {   // A <- A G (columns p, q)
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {   // A <- G^T A (rows p, q)
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int k = 0; k < 3; ++k) ev[k] = a[k][k];
+}
+
+int cell_strain(const double lattice0[3][3], const double lattice[3][3], double &eps_max, double &dvol)
+{
+    const int n1[3] = {1, 1, 1};
+    Metric m0, m;
+    int e = make_metric(lattice0, n1, m0);
+    if (e) return e;
+    if ((e = make_metric(lattice, n1, m))) return e;
+    double F[3][3], E[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) F[a][b] = m.h[a][0] * m0.hinv[0][b] + m.h[a][1] * m0.hinv[1][b] + m.h[a][2] * m0.hinv[2][b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            E[a][b] = 0.5 * (F[0][a] * F[0][b] + F[1][a] * F[1][b] + F[2][a] * F[2][b] - (a == b ? 1.0 : 0.0));
+    double ev[3];
+    sym3_eigenvalues(E, ev);
+    eps_max = std::max(std::fabs(ev[0]), std::max(std::fabs(ev[1]), std::fabs(ev[2])));
+    dvol = m.vol / m0.vol - 1.0;
+    return EXX_OK;
+}
+
 // r = h (m / N): the offset vector of a grid step, fixed operation order.
 static inline void step_vec(const Metric &mt, const int *m, double *r)
 {

@@ -26,6 +26,12 @@ struct Metric {
 };
 int make_metric(const double lattice[3][3], const int n[3], Metric &m);
 
+// Green-Lagrange strain of a cell relative to a reference cell (both as
+// lattice rows): F = h h0^-1, E = (F^T F - I) / 2.  eps_max = the largest
+// |eigenvalue| of E, dvol = det F - 1.  Frozen proto-subdomains deform with the
+// cell (Sec. III B 2); this is the criterion for re-assembling them.
+int cell_strain(const double lattice0[3][3], const double lattice[3][3], double &eps_max, double &dvol);
+
 // Pure-derivative directions of the NK Laplacian (Eq. lapG_mod_nk3d): the three
 // lattice axes and n_aux auxiliary grid directions.
 struct Stencil {

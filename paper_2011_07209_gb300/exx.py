@@ -28,7 +28,7 @@ _lock = threading.Lock()
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
            "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version",
-           "exx_pair_list_noalloc", "exx_ctx_set_solver")
+           "exx_pair_list_noalloc", "exx_ctx_set_solver", "exx_cell_strain")
 
 
 class Cell(C.Structure):
@@ -106,6 +106,7 @@ def lib(build_if_missing: bool = False):
                                                 C.POINTER(Orbitals), C.POINTER(Result), C.c_void_p]
             L.exx_get_pair_list.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.exx_dbox_halfwidth.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(C.c_int)]
+            L.exx_cell_strain.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.exx_ctx_set_timing.argtypes = [C.c_void_p, C.c_int]
             L.exx_ctx_set_solver.argtypes = [C.c_void_p, C.c_int]
             L.exx_pair_list_noalloc.argtypes = [C.POINTER(Cell), C.c_void_p, C.c_int, C.c_double, C.c_int,
@@ -155,6 +156,38 @@ def dbox_halfwidth(lattice, n, params: Params):
     hw = (C.c_int * 3)()
     _check(lib().exx_dbox_halfwidth(C.byref(make_cell(lattice, n)), C.byref(params), hw), "exx_dbox_halfwidth")
     return np.array(list(hw), np.int64)
+
+
+def cell_strain(lattice0, lattice):
+    """(largest |principal Green-Lagrange strain|, relative volume change) of
+    `lattice` relative to `lattice0` (rows are lattice vectors)."""
+    a = (C.c_double * 9)(*[float(x) for x in np.asarray(lattice0, float).ravel()])
+    b = (C.c_double * 9)(*[float(x) for x in np.asarray(lattice, float).ravel()])
+    out = (C.c_double * 2)()
+    _check(lib().exx_cell_strain(a, b, out), "exx_cell_strain")
+    return float(out[0]), float(out[1])
+
+
+class Reassembly:
+    """When to re-assemble frozen proto-subdomains from scratch (Sec. III B 2):
+    once the strain of the current cell relative to the plan's reference cell
+    exceeds `eps_max` (largest principal Green-Lagrange strain), or every
+    `stride` steps since the last assembly (0: no stride).  Re-assembling
+    means creating a new Plan whose reference cell is the current one; its
+    pairs start without a warm start (their offsets changed)."""
+
+    def __init__(self, eps_max=None, stride=0):
+        if eps_max is not None and not eps_max > 0.0:
+            raise ValueError("eps_max must be positive")
+        if stride < 0:
+            raise ValueError("stride must be >= 0")
+        self.eps_max = eps_max
+        self.stride = int(stride)
+
+    def due(self, lattice0, lattice, steps_since: int) -> bool:
+        if self.stride and steps_since >= self.stride:
+            return True
+        return self.eps_max is not None and cell_strain(lattice0, lattice)[0] > self.eps_max
 
 
 def dbox_layout(lattice, n, centres, params: Params, dbox=None):
