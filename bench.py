@@ -319,7 +319,7 @@ def run_gpu(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD + (f" [profiling subset: first {args.subset} MLWFs]" if args.subset else ""),
                        "pairs_per_step": n_pairs, "n_pe": info["n_pe_pair"],
                        "n_me": info["n_me_pair"], "n_stcl": info["n_stcl"],
-                       "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_fp64_residuals": tot_ref / max(n_pairs, 1),
+                       "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_true_residuals": tot_ref / max(n_pairs, 1),
                        "ctas": info["ctas"], "threads": info["threads"], "ctas_per_pair": info["cluster"],
                        "l2": "inputs larger than L2 (orbital boxes 512 MB, D_xx 3.5 GB per step)",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
@@ -432,7 +432,7 @@ def run_workload(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == exx.FP64 else "mixed-f32-f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "pairs_per_step": n_pairs / args.steps,
-                   "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_fp64_residuals": tot_ref / max(n_pairs, 1),
+                   "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_true_residuals": tot_ref / max(n_pairs, 1),
                    "warm_started_pairs_per_step": n_warm / args.steps,
                    "warm_start": args.workload == "trajectory256" and not args.cold},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
