@@ -248,6 +248,18 @@ int exx_get_pair_list(exx_plan *plan, int cap, int *n, int *rows);
 int exx_pair_list_noalloc(const exx_cell *cell, const double *centres, int n_orb, double r_pair, int cap,
                           int *rows, int *n_pairs, void *stream);
 
+/* The geometry that a plan for this cell and these parameters would have,
+ * computed on the host with no device work or allocation (for example to size
+ * buffers before exx_plan_create): the proto-subdomain point counts and dense
+ * CG boxes of self and non-self pairs (Sec. III B), and the NK stencil of the
+ * cell (Sec. III C, Algorithm 1).  Fills n_pe_*, n_me_*, n_halo_*, box_*,
+ * n_aux, n_stcl, dirs, coef and aux_frozen (the auxiliary directions chosen
+ * for this cell) as exx_plan_query does for a plan created at this cell; the
+ * solver fields (workspace_bytes, pair_capacity, ctas, threads, cluster) are
+ * zero.  Errors: EXX_ERR_ARG (null pointer or invalid parameters),
+ * EXX_ERR_CELL, EXX_ERR_NK, EXX_ERR_HALO, as exx_plan_create. */
+int exx_geometry_query(const exx_cell *cell, const exx_params *params, exx_plan_info *info);
+
 /* Index half-widths of a D box that holds every contribution of the pairs of
  * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);

@@ -716,6 +716,39 @@ int exx_plan_query(const exx_plan *p, exx_plan_info *info)
     return EXX_OK;
 }
 
+int exx_geometry_query(const exx_cell *cell, const exx_params *params, exx_plan_info *info)
+{
+    if (!cell || !params || !info) return EXX_ERR_ARG;
+    int e = check_params(params);
+    if (e) return e;
+    Metric m;
+    if ((e = make_metric(cell->lattice, cell->n, m))) return e;
+    Stencil st;
+    if ((e = make_stencil(m, params->fd_order, params->nq, nullptr, 0, st))) return e;
+    std::memset(info, 0, sizeof(*info));
+    const double rpe[2] = {params->r_pe_self, params->r_pe_pair};
+    const double rme[2] = {params->r_me_self, params->r_me_pair};
+    for (int s = 0; s < 2; ++s) {
+        OffsetSet o;
+        if ((e = make_offsets(m, rpe[s], rme[s], o))) return e;
+        SetLayout L;
+        if ((e = make_layout(o, st, params->fd_order, L))) return e;
+        (s ? info->n_pe_pair : info->n_pe_self) = L.n_pe;
+        (s ? info->n_me_pair : info->n_me_self) = L.n_pe + L.n_shell;
+        (s ? info->n_halo_pair : info->n_halo_self) = L.n_halo;
+        for (int a = 0; a < 3; ++a) (s ? info->box_pair : info->box_self)[a] = L.B[a];
+    }
+    info->n_aux = st.n_aux;
+    info->n_stcl = 2 * params->fd_order * st.ndir + 1;
+    for (int d = 0; d < 6; ++d) {
+        for (int k = 0; k < 3; ++k) info->dirs[d][k] = d < st.ndir ? st.dir[d][k] : 0;
+        info->coef[d] = d < st.ndir ? st.coef[d] : 0.0;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) info->aux_frozen[a][k] = a < st.n_aux ? st.dir[3 + a][k] : 0;
+    return EXX_OK;
+}
+
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int hw[3])
 {
     if (!cell || !params || !hw) return EXX_ERR_ARG;

@@ -28,7 +28,7 @@ _lock = threading.Lock()
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
            "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version",
-           "exx_pair_list_noalloc", "exx_ctx_set_solver", "exx_cell_strain")
+           "exx_pair_list_noalloc", "exx_ctx_set_solver", "exx_cell_strain", "exx_geometry_query")
 
 
 class Cell(C.Structure):
@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = False):
             L.exx_get_pair_list.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.exx_dbox_halfwidth.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(C.c_int)]
             L.exx_cell_strain.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.exx_geometry_query.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(PlanInfo)]
             L.exx_ctx_set_timing.argtypes = [C.c_void_p, C.c_int]
             L.exx_ctx_set_solver.argtypes = [C.c_void_p, C.c_int]
             L.exx_pair_list_noalloc.argtypes = [C.POINTER(Cell), C.c_void_p, C.c_int, C.c_double, C.c_int,
@@ -245,6 +246,27 @@ class Context:
             pass
 
 
+def _info_dict(pi: PlanInfo) -> dict:
+    return {
+        "n_pe_self": pi.n_pe_self, "n_me_self": pi.n_me_self, "n_pe_pair": pi.n_pe_pair,
+        "n_me_pair": pi.n_me_pair, "n_halo_self": pi.n_halo_self, "n_halo_pair": pi.n_halo_pair,
+        "n_aux": pi.n_aux, "n_stcl": pi.n_stcl,
+        "dirs": np.array(list(pi.dirs)).reshape(6, 3)[:3 + pi.n_aux], "coef": np.array(list(pi.coef))[:3 + pi.n_aux],
+        "aux": np.array(list(pi.aux_frozen)).reshape(3, 3)[:pi.n_aux],
+        "box_self": list(pi.box_self), "box_pair": list(pi.box_pair), "workspace_bytes": pi.workspace_bytes,
+        "pair_capacity": pi.pair_capacity, "ctas": pi.ctas, "threads": pi.threads, "cluster": pi.cluster,
+    }
+
+
+def geometry(lattice, n, params: Params) -> dict:
+    """Geometry of a plan at this cell (point counts, dense boxes, NK stencil),
+    computed on the host without a GPU; solver fields are zero."""
+    pi = PlanInfo()
+    _check(lib().exx_geometry_query(C.byref(make_cell(lattice, n)), C.byref(params), C.byref(pi)),
+           "exx_geometry_query")
+    return _info_dict(pi)
+
+
 class Plan:
     def __init__(self, ctx: Context, lattice, n, params: Params, max_orb: int, box):
         self.ctx = ctx
@@ -258,14 +280,7 @@ class Plan:
     def info(self) -> dict:
         pi = PlanInfo()
         _check(lib().exx_plan_query(self.handle, C.byref(pi)), "exx_plan_query")
-        return {
-            "n_pe_self": pi.n_pe_self, "n_me_self": pi.n_me_self, "n_pe_pair": pi.n_pe_pair,
-            "n_me_pair": pi.n_me_pair, "n_halo_self": pi.n_halo_self, "n_halo_pair": pi.n_halo_pair,
-            "n_aux": pi.n_aux, "n_stcl": pi.n_stcl,
-            "dirs": np.array(list(pi.dirs)).reshape(6, 3)[:3 + pi.n_aux], "coef": np.array(list(pi.coef))[:3 + pi.n_aux],
-            "box_self": list(pi.box_self), "box_pair": list(pi.box_pair), "workspace_bytes": pi.workspace_bytes,
-            "pair_capacity": pi.pair_capacity, "ctas": pi.ctas, "threads": pi.threads, "cluster": pi.cluster,
-        }
+        return _info_dict(pi)
 
     def pair_list(self) -> np.ndarray:
         n = C.c_int()
