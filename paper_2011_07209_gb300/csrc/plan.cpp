@@ -588,4 +588,169 @@ int make_cluster_part(const SetLayout &L, const Stencil &st, int fd_n, int nc, C
     return EXX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multigrid hierarchy (see plan.h).
+// ---------------------------------------------------------------------------
+
+// Parents of a box coordinate u along one axis: (coarse coordinate, weight).
+static inline int mg_parents(int u, int *c, double *w)
+{
+    if ((u & 1) == 0) {
+        c[0] = u >> 1;
+        w[0] = 1.0;
+        return 1;
+    }
+    c[0] = u >> 1;
+    c[1] = (u >> 1) + 1;
+    w[0] = w[1] = 0.5;
+    return 2;
+}
+
+// Level l + 1 from level l: active coarse points, then A_c = P^T A P
+// accumulated per coarse row in a dense window of coarse offsets.
+static int mg_coarsen(const MgLevel &f, MgLevel &c)
+{
+    for (int a = 0; a < 3; ++a) c.B[a] = f.B[a] / 2 + 1;
+    const long long cbox = (long long)c.B[0] * c.B[1] * c.B[2];
+    c.idx.assign((size_t)cbox, -1);
+    auto coords = [](const int *B, long long o, int *u) {
+        u[2] = (int)(o % B[2]);
+        u[1] = (int)((o / B[2]) % B[1]);
+        u[0] = (int)(o / ((long long)B[1] * B[2]));
+    };
+    // parents of every fine point (at most 8), and the active coarse set
+    std::vector<int32_t> pc((size_t)f.n * 8, -1);
+    std::vector<double> pw((size_t)f.n * 8, 0.0);
+    std::vector<long long> pbox((size_t)f.n * 8, -1);
+    for (int i = 0; i < f.n; ++i) {
+        int u[3], cc[3][2];
+        double ww[3][2];
+        int np[3];
+        coords(f.B, f.pts[i], u);
+        for (int a = 0; a < 3; ++a) np[a] = mg_parents(u[a], cc[a], ww[a]);
+        int k = 0;
+        for (int x = 0; x < np[0]; ++x)
+            for (int y = 0; y < np[1]; ++y)
+                for (int z = 0; z < np[2]; ++z, ++k) {
+                    const long long o = ((long long)cc[0][x] * c.B[1] + cc[1][y]) * c.B[2] + cc[2][z];
+                    pbox[(size_t)i * 8 + k] = o;
+                    pw[(size_t)i * 8 + k] = ww[0][x] * ww[1][y] * ww[2][z];
+                    c.idx[(size_t)o] = 0;
+                }
+    }
+    c.pts.clear();
+    for (long long o = 0; o < cbox; ++o)
+        if (c.idx[(size_t)o] == 0) {
+            c.idx[(size_t)o] = (int32_t)c.pts.size();
+            c.pts.push_back((int32_t)o);
+        }
+    c.n = (int)c.pts.size();
+    for (size_t k = 0; k < pc.size(); ++k)
+        if (pbox[k] >= 0) pc[k] = c.idx[(size_t)pbox[k]];
+    // coarse reach: a fine operator of reach r couples parents at most (r + 2) / 2 apart
+    int reach = 0;
+    for (int i = 0; i < f.n; ++i) {
+        int u[3];
+        coords(f.B, f.pts[i], u);
+        for (int k = f.row[i]; k < f.row[i + 1]; ++k) {
+            int v[3];
+            coords(f.B, f.pts[f.col[k]], v);
+            for (int a = 0; a < 3; ++a) reach = std::max(reach, std::abs(v[a] - u[a]));
+        }
+    }
+    const int R = (reach + 2) / 2, W = 2 * R + 1;
+    std::vector<double> win((size_t)c.n * W * W * W, 0.0);
+    for (int i = 0; i < f.n; ++i)
+        for (int k = f.row[i]; k < f.row[i + 1]; ++k) {
+            const int j = f.col[k];
+            const double a = f.val[k];
+            for (int p = 0; p < 8; ++p) {
+                const int ci = pc[(size_t)i * 8 + p];
+                if (ci < 0) continue;
+                int uc[3];
+                coords(c.B, c.pts[ci], uc);
+                const double wi = pw[(size_t)i * 8 + p] * a;
+                for (int q = 0; q < 8; ++q) {
+                    const int cj = pc[(size_t)j * 8 + q];
+                    if (cj < 0) continue;
+                    int vc[3];
+                    coords(c.B, c.pts[cj], vc);
+                    const int dx = vc[0] - uc[0] + R, dy = vc[1] - uc[1] + R, dz = vc[2] - uc[2] + R;
+                    if (dx < 0 || dx >= W || dy < 0 || dy >= W || dz < 0 || dz >= W) return EXX_ERR_ARG;
+                    win[(((size_t)ci * W + dx) * W + dy) * W + dz] += wi * pw[(size_t)j * 8 + q];
+                }
+            }
+        }
+    c.row.assign((size_t)c.n + 1, 0);
+    c.col.clear();
+    c.val.clear();
+    for (int ci = 0; ci < c.n; ++ci) {
+        int uc[3];
+        coords(c.B, c.pts[ci], uc);
+        std::vector<std::pair<int, double>> r;
+        for (int dx = 0; dx < W; ++dx)
+            for (int dy = 0; dy < W; ++dy)
+                for (int dz = 0; dz < W; ++dz) {
+                    const double v = win[(((size_t)ci * W + dx) * W + dy) * W + dz];
+                    if (v == 0.0) continue;
+                    const int x = uc[0] + dx - R, y = uc[1] + dy - R, z = uc[2] + dz - R;
+                    const int cj = c.idx[((size_t)x * c.B[1] + y) * c.B[2] + z];
+                    r.push_back({cj, v});
+                }
+        std::sort(r.begin(), r.end());
+        for (const auto &e : r) {
+            c.col.push_back(e.first);
+            c.val.push_back(e.second);
+        }
+        c.row[ci + 1] = (int32_t)c.col.size();
+    }
+    return EXX_OK;
+}
+
+int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_points, std::vector<MgLevel> &lv)
+{
+    lv.clear();
+    if (fd_n < 1 || fd_n > kMaxFd || min_points < 1) return EXX_ERR_ARG;
+    double w2[kMaxFd + 1], w1[kMaxFd + 1];
+    fd_weights(fd_n, w2, w1);
+    MgLevel f;
+    for (int a = 0; a < 3; ++a) f.B[a] = L.B[a];
+    f.n = L.n_pe;
+    f.idx.assign((size_t)L.box, -1);
+    f.pts = L.pe_off;
+    for (int i = 0; i < f.n; ++i) f.idx[(size_t)L.pe_off[i]] = i;
+    // A = -L: centre -sum_d coef_d w2[0], neighbours -coef_d w2[|q|] (PE only)
+    double centre = 0.0;
+    for (int d = 0; d < st.ndir; ++d) centre += st.coef[d] * w2[0];
+    f.row.assign((size_t)f.n + 1, 0);
+    for (int i = 0; i < f.n; ++i) {
+        std::vector<std::pair<int, double>> r;
+        r.push_back({i, -centre});
+        for (int d = 0; d < st.ndir; ++d)
+            for (int q = 1; q <= fd_n; ++q)
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    const long long o = (long long)L.pe_off[i] + (long long)sg * q * L.dstride[d];
+                    if (o < 0 || o >= L.box) continue;
+                    const int j = f.idx[(size_t)o];
+                    if (j >= 0) r.push_back({j, -st.coef[d] * w2[q]});
+                }
+        std::sort(r.begin(), r.end());
+        for (const auto &e : r) {
+            f.col.push_back(e.first);
+            f.val.push_back(e.second);
+        }
+        f.row[i + 1] = (int32_t)f.col.size();
+    }
+    lv.push_back(std::move(f));
+    while (lv.back().n > min_points) {
+        MgLevel c;
+        const int e = mg_coarsen(lv.back(), c);
+        if (e) return e;
+        if (c.n >= lv.back().n) break;   // no reduction (degenerate box): stop
+        lv.push_back(std::move(c));
+    }
+    return EXX_OK;
+}
+
 }  // namespace exx
+

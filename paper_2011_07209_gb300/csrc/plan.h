@@ -76,6 +76,27 @@ struct SetLayout {
 };
 int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
 
+// Multigrid hierarchy of one proto-subdomain, for preconditioning the Step IV
+// CG (not in the paper, which uses plain CG: the preconditioner changes the
+// iterates, not the discrete equations or the stopping rule).  Level 0: the PE
+// points of the dense CG box with A = -L, the NK stencil with the halo moved to
+// the right-hand side (Dirichlet zero).  Level l + 1: the points of a box half
+// as fine that are parents of active level-l points, where a point at box
+// coordinate u has the parents floor(u/2) and ceil(u/2) along each axis
+// (trilinear prolongation, weight 1 on an even coordinate and 1/2 on each side of
+// an odd one), restriction its transpose, and the Galerkin operator
+// A_{l+1} = P^T A_l P.  Operators are CSR with columns sorted.
+struct MgLevel {
+    int B[3] = {};                 // box of the level (level 0: the dense CG box)
+    int n = 0;                     // active points
+    std::vector<int32_t> idx;      // box point -> active index, -1 when inactive
+    std::vector<int32_t> pts;      // active index -> box point
+    std::vector<int32_t> row, col; // CSR of A_l
+    std::vector<double> val;
+};
+// Levels until one has at most min_points points (that one included).
+int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_points, std::vector<MgLevel> &lv);
+
 // Row partition of one set over a cluster of nc CTAs (the cluster CG path).
 // The box rows (plane z, row y) that hold PE or halo points are taken in
 // (z, y) order and split into nc contiguous ranges with about equal numbers of
