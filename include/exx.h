@@ -242,9 +242,12 @@ int exx_get_pair_list(exx_plan *plan, int cap, int *n, int *rows);
  * that loads the library until the process exits; larger n_orb returns
  * EXX_ERR_CAPACITY.  The first call on a device resolves that array's device
  * address (cudaGetSymbolAddress) and should come before any stream capture.
- * Every call shares the array, so calls that overlap on the GPU (on
- * different streams, or from different threads) race.  The work is enqueued
- * on `stream` and the call returns without waiting for it. */
+ * The address is resolved again when the current context changes (for
+ * instance after cudaDeviceReset).  Every call shares the array, so calls
+ * that overlap on the GPU (on different streams, or from different threads)
+ * race.  A CUDA error left pending by the caller's earlier work is returned
+ * as EXX_ERR_CUDA and left pending (not cleared).  The work is enqueued on
+ * `stream` and the call returns without waiting for it. */
 int exx_pair_list_noalloc(const exx_cell *cell, const double *centres, int n_orb, double r_pair, int cap,
                           int *rows, int *n_pairs, void *stream);
 

@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 def _sources():
     return [os.path.join(SRC, f) for f in CU_SOURCES + CPP_SOURCES] + \
-        [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")] + [os.path.join(INCLUDE, "exx.h")]
+        [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))] + [os.path.join(INCLUDE, "exx.h")]
 
 
 def up_to_date() -> bool:

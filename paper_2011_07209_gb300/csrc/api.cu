@@ -28,6 +28,13 @@ int cuda_fail(cudaError_t e, int line)
 }
 }  // namespace
 
+int exx::note_cuda_error(const char *where, cudaError_t e)
+{
+    std::snprintf(g_err_detail, sizeof(g_err_detail), "%s: %s (%s)", where, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return EXX_ERR_CUDA;
+}
+
 #define CK(call)                                              \
     do {                                                      \
         cudaError_t e_ = (call);                              \

@@ -16,6 +16,7 @@
 
 #include "exx_dev.h"
 #include "kernels.h"
+#include "pair_rule.cuh"
 
 namespace exx {
 
@@ -125,57 +126,8 @@ __global__ void k_tables(const CellDev *__restrict__ cell, int which, double *S6
 }
 
 // ---------------------------------------------------------------------------
-// Pair list.  For i <= j: s = h^-1 C (row sums left to right, no FMA);
-// ds = s_j - s_i - round(ds); image k in {-1,0,1}^3 with the smallest |h(ds+k)|^2
-// (first in lexicographic k on ties); kept when that is <= R_pair^2.  Centre
-// g = NINT(N (s_i + (ds + k)/2)) mod N, NINT rounding half away from zero.
-// These operations and their order are the written rule the oracle follows
-// too, so both lists agree bit for bit.
+// Pair list: the rule of pair_rule.cuh, one CTA per orbital row.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dot3_rn(const double *r, double a, double b, double c)
-{
-    return __dadd_rn(__dadd_rn(__dmul_rn(r[0], a), __dmul_rn(r[1], b)), __dmul_rn(r[2], c));
-}
-
-__device__ bool pair_test(const CellDev &C, int i, int j, int *kb, int *g)
-{
-    const double *ci = C.centres + 3 * i, *cj = C.centres + 3 * j;
-    double si[3], ds[3];
-    for (int al = 0; al < 3; ++al) {
-        si[al] = dot3_rn(C.hinv[al], ci[0], ci[1], ci[2]);
-        const double sj = dot3_rn(C.hinv[al], cj[0], cj[1], cj[2]);
-        const double d = __dadd_rn(sj, -si[al]);
-        ds[al] = __dadd_rn(d, -round(d));
-    }
-    double best = 1.0 / 0.0;
-    kb[0] = kb[1] = kb[2] = 0;
-    for (int k0 = -1; k0 <= 1; ++k0)
-        for (int k1 = -1; k1 <= 1; ++k1)
-            for (int k2 = -1; k2 <= 1; ++k2) {
-                const double t0 = __dadd_rn(ds[0], (double)k0), t1 = __dadd_rn(ds[1], (double)k1),
-                             t2 = __dadd_rn(ds[2], (double)k2);
-                const double d0 = dot3_rn(C.h[0], t0, t1, t2);
-                const double d1 = dot3_rn(C.h[1], t0, t1, t2);
-                const double d2 = dot3_rn(C.h[2], t0, t1, t2);
-                const double dd = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                if (dd < best) {
-                    best = dd;
-                    kb[0] = k0;
-                    kb[1] = k1;
-                    kb[2] = k2;
-                }
-            }
-    if (!(best <= C.r_pair2)) return false;
-    for (int al = 0; al < 3; ++al) {
-        const double sm = __dadd_rn(si[al], __dmul_rn(__dadd_rn(ds[al], (double)kb[al]), 0.5));
-        const long long gg = (long long)round(__dmul_rn((double)C.n[al], sm));
-        long long r = gg % C.n[al];
-        if (r < 0) r += C.n[al];
-        g[al] = (int)r;
-    }
-    return true;
-}
-
 // One CTA of kRowThreads per orbital row (cell, i).  fill = 0: count; 1: write.
 __global__ void __launch_bounds__(kRowThreads) k_pair_rows(const CellDev *__restrict__ cells, int n_cells,
                                                           ListDev L, int fill)
@@ -194,7 +146,7 @@ __global__ void __launch_bounds__(kRowThreads) k_pair_rows(const CellDev *__rest
     for (int j0 = i; j0 < C.n_orb; j0 += kRowThreads) {
         const int j = j0 + threadIdx.x;
         int kb[3], g[3];
-        const bool ok = (j < C.n_orb) && pair_test(C, i, j, kb, g);
+        const bool ok = (j < C.n_orb) && pair_rule(C, i, j, kb, g);
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (lane == 0) warp_tot[w] = __popc(bal);
         __syncthreads();

@@ -53,6 +53,9 @@ int cluster_capacity_bytes();
 // Launches as many clusters as can be resident (at most slots.n_slots); *n_clusters receives the count.
 cudaError_t launch_solve_cluster(const CellDev *cells, const ListDev &L, const SolveSlots &slots, int rowtab_words,
                                  int p_floats, int max_groups, int inner_shift, int *n_clusters, cudaStream_t s);
+// Records the CUDA error behind an EXX_ERR_CUDA for exx_last_error_detail()
+// (thread-local) and returns EXX_ERR_CUDA.
+int note_cuda_error(const char *where, cudaError_t e);
 cudaError_t launch_warm_map(const PairRec *rows, int n, int n_orb, int *map, cudaStream_t s);
 
 }  // namespace exx

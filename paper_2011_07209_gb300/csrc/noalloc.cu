@@ -14,8 +14,11 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/exx.h"
+#include "kernels.h"
+#include "pair_rule.cuh"
 #include "plan.h"
 
 namespace {
@@ -35,50 +38,6 @@ struct PairCell {
     int n_orb;
 };
 
-__device__ __forceinline__ double dot3(const double *r, double a, double b, double c)
-{
-    return __dadd_rn(__dadd_rn(__dmul_rn(r[0], a), __dmul_rn(r[1], b)), __dmul_rn(r[2], c));
-}
-
-// The written rule of the pair list: s = h^-1 C, ds = s_j - s_i - round(ds), the
-// lattice image k in {-1,0,1}^3 (lexicographic, first minimum) with the smallest
-// |h(ds+k)|^2, kept when <= R_pair^2; centre g = NINT(N (s_i + (ds+k)/2)) mod N.
-__device__ bool pair_rule(const PairCell &C, int i, int j, int *kb, int *g)
-{
-    const double *ci = C.centres + 3 * i, *cj = C.centres + 3 * j;
-    double si[3], ds[3];
-    for (int a = 0; a < 3; ++a) {
-        si[a] = dot3(C.hinv[a], ci[0], ci[1], ci[2]);
-        const double d = __dadd_rn(dot3(C.hinv[a], cj[0], cj[1], cj[2]), -si[a]);
-        ds[a] = __dadd_rn(d, -round(d));
-    }
-    double best = 1.0 / 0.0;
-    kb[0] = kb[1] = kb[2] = 0;
-    for (int k0 = -1; k0 <= 1; ++k0)
-        for (int k1 = -1; k1 <= 1; ++k1)
-            for (int k2 = -1; k2 <= 1; ++k2) {
-                const double t0 = __dadd_rn(ds[0], (double)k0), t1 = __dadd_rn(ds[1], (double)k1),
-                             t2 = __dadd_rn(ds[2], (double)k2);
-                const double d0 = dot3(C.h[0], t0, t1, t2), d1 = dot3(C.h[1], t0, t1, t2),
-                             d2 = dot3(C.h[2], t0, t1, t2);
-                const double dd = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                if (dd < best) {
-                    best = dd;
-                    kb[0] = k0;
-                    kb[1] = k1;
-                    kb[2] = k2;
-                }
-            }
-    if (!(best <= C.r_pair2)) return false;
-    for (int a = 0; a < 3; ++a) {
-        const double sm = __dadd_rn(si[a], __dmul_rn(__dadd_rn(ds[a], (double)kb[a]), 0.5));
-        long long r = (long long)round(__dmul_rn((double)C.n[a], sm)) % C.n[a];
-        if (r < 0) r += C.n[a];
-        g[a] = (int)r;
-    }
-    return true;
-}
-
 // One CTA per row i; fill = 0 counts, fill = 1 writes rows in (i, j) order.
 __global__ void __launch_bounds__(kThreads) k_rows_noalloc(PairCell C, int *scratch, int fill, int cap, int *rows)
 {
@@ -91,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_noalloc(PairCell C, int *scra
     for (int j0 = i; j0 < C.n_orb; j0 += kThreads) {
         const int j = j0 + threadIdx.x;
         int kb[3], g[3];
-        const bool ok = (j < C.n_orb) && pair_rule(C, i, j, kb, g);
+        const bool ok = (j < C.n_orb) && exx::pair_rule(C, i, j, kb, g);
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (lane == 0) warp_tot[w] = __popc(bal);
         __syncthreads();
@@ -151,8 +110,46 @@ __global__ void __launch_bounds__(1024) k_scan_noalloc(int *scratch, int n_rows,
     }
 }
 
-// Device address of the static scratch, resolved once per device.
-int *g_scratch_addr[64] = {};
+// Device address of the static scratch, resolved once per device and context.
+// The address belongs to the module loaded into one CUDA context: if the caller
+// resets the device (cudaDeviceReset) and the primary context is created anew,
+// the module is loaded again at another address, so the cached address is
+// keyed on the context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry-point query so that the library does not link libcuda).
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    int *ptr;
+};
+ScratchAddr g_scratch_addr[64] = {};
+std::mutex g_scratch_mu;
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 on failure).
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f2;
+        cudaGetLastError();
+        tried = true;
+    }
+    if (!get_current || !get_id) return 0;
+    void *c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -165,20 +162,34 @@ extern "C" int exx_pair_list_noalloc(const exx_cell *cell, const double *centres
     exx::Metric m;
     const int e = exx::make_metric(cell->lattice, cell->n, m);
     if (e) return e;
+    // an error left pending by the caller's earlier work is reported, not cleared
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return exx::note_cuda_error("noalloc.cu: pending error at entry", pending);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
         cudaGetLastError();
-        return EXX_ERR_CUDA;
+        return exx::note_cuda_error("noalloc.cu: cudaGetDevice", ce);
     }
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_pairlist_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return EXX_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return EXX_ERR_ARG;
+    int *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        ScratchAddr &sa = g_scratch_addr[dev];
+        const unsigned long long ctx_id = current_ctx_id();   // 0: no context current yet
+        if (!sa.ptr || ctx_id == 0 || sa.ctx_id != ctx_id) {
+            void *p = nullptr;
+            ce = cudaGetSymbolAddress(&p, g_pairlist_scratch);   // loads the module if needed
+            if (ce != cudaSuccess || !p) {
+                cudaGetLastError();
+                sa.ptr = nullptr;
+                return exx::note_cuda_error("noalloc.cu: cudaGetSymbolAddress", ce);
+            }
+            sa.ptr = (int *)p;
+            sa.ctx_id = current_ctx_id();
         }
-        g_scratch_addr[dev] = (int *)p;
+        scratch = sa.ptr;
     }
-    int *scratch = g_scratch_addr[dev];
     PairCell C;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -190,11 +201,11 @@ extern "C" int exx_pair_list_noalloc(const exx_cell *cell, const double *centres
     C.centres = centres;
     C.n_orb = n_orb;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaGetLastError();
     // the counts of every row are rewritten below; nothing else needs zeroing
     if (n_orb > 0) k_rows_noalloc<<<n_orb, kThreads, 0, s>>>(C, scratch, 0, cap, rows);
     k_scan_noalloc<<<1, 1024, 0, s>>>(scratch, n_orb, n_pairs);
     if (n_orb > 0) k_rows_noalloc<<<n_orb, kThreads, 0, s>>>(C, scratch, 1, cap, rows);
-    if (cudaGetLastError() != cudaSuccess) return EXX_ERR_CUDA;
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return exx::note_cuda_error("noalloc.cu: launch", ce);
     return EXX_OK;
 }

@@ -42,6 +42,22 @@ def test_noalloc_pair_list_matches_solve(case):
             assert k == ref.shape[0], (name, call)
             assert np.array_equal(rows[:k].cpu().numpy(), ref), (name, call)
             assert np.all(rows[k:].cpu().numpy() == -7)
+        # a capacity below the pair count: the first cap rows are written, the
+        # rest of the buffer is untouched and the count is still the full one
+        cap2 = max(1, k // 3)
+        rows = torch.full((cap2 + 5, 8), -7, dtype=torch.int32, device="cuda")
+        n.fill_(-1)
+        assert exx.pair_list_noalloc(ws.lattice, ws.n, cen, ws.n_orb, r_pair, rows[:cap2], n) == exx.OK
+        torch.cuda.synchronize()
+        assert int(n.item()) == k
+        assert np.array_equal(rows[:cap2].cpu().numpy(), ref[:cap2])
+        assert np.all(rows[cap2:].cpu().numpy() == -7)
+        # no orbitals: zero pairs, nothing written
+        n.fill_(-1)
+        assert exx.pair_list_noalloc(ws.lattice, ws.n, cen, 0, r_pair, rows, n) == exx.OK
+        torch.cuda.synchronize()
+        assert int(n.item()) == 0
+        assert np.all(rows.cpu().numpy() == -7)
         # sizes beyond the static scratch are refused
         big = torch.zeros((16385, 3), dtype=torch.float64, device="cuda")
         assert exx.pair_list_noalloc(ws.lattice, ws.n, big, 16385, r_pair, rows, n) == exx.ERR_CAPACITY
