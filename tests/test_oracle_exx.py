@@ -219,3 +219,66 @@ def test_edge_cases():
     with pytest.raises(oracle.OracleError) as e:
         oracle.exx(g, oracle.make_params(r_pe=4.0, r_me=5.5, max_iter=3), want_d=False)
     assert e.value.code == 5
+
+
+@pytest.mark.parametrize("cell", ["cubic", "triclinic"])
+def test_cg_matches_dense_direct_solve(cell):
+    """Step IV on a tiny subdomain: the oracle's CG potential equals the direct
+    solution of the dense system A v = 4 pi rho + L_shell v_shell (Eq. pe with
+    the Dirichlet data of Eq. me), where A = -L restricted to PE is assembled
+    here from the stencil's directions, coefficients and weights (Eqs. d2_1,
+    lapG_mod_nk3d).  The pair density is non-spherical (a != 0 orbitals, i != j),
+    so moments with l > 0 feed the boundary values."""
+    if cell == "cubic":
+        lat = np.diag([7.0, 7.0, 7.0])
+    else:
+        lat = 7.0 * np.array([[1.0, 0, 0], [0.1, 1.0, 0], [0.05, -0.08, 1.0]])
+    n = (35, 35, 35)
+    ws = synth.water_cell(lat, n, 1, 11, r_phi=3.0)
+    r_pe, r_me = 1.1, 2.4
+    p = oracle.make_params(r_pair=4.0, r_pe=r_pe, r_me=r_me, tol=1e-13, lmax=6)
+    rows = oracle.pair_list(ws.lattice, ws.n, ws.centres, 4.0)
+    i, j, g = 0, 1, None
+    for r in rows:
+        if r[0] == i and r[1] == j:
+            g = np.asarray(r[5:8])
+    assert g is not None
+    out = oracle.pair_potential(ws, i, j, g, p)
+    npe, m = out["n_pe"], out["m"]
+    assert 300 < npe < 1200
+    nn = np.asarray(n)
+    h = ws.lattice.T
+    # pair density on PE from the orbital boxes
+    def phi_at(k, pts):
+        u = (pts - ws.box_lo[k]) % nn
+        ok = np.all(u < ws.box, axis=1)
+        v = np.zeros(len(pts))
+        v[ok] = ws.phi[k][u[ok, 0], u[ok, 1], u[ok, 2]]
+        return v
+    pts = (g + m) % nn
+    rho = (phi_at(i, pts) * phi_at(j, pts))[:npe]
+    # the far field on the shell is the oracle's multipole expansion (pinned separately)
+    rbar = (m / nn) @ h.T
+    Q = oracle.multipoles(6, rbar[:npe], rho * ws.dv)
+    assert np.abs(Q[1:]).max() > 1e-3 * abs(Q[0])       # l > 0 moments matter here
+    v_sh = oracle.farfield(6, Q, rbar[npe:])
+    assert np.allclose(out["v"][npe:], v_sh, rtol=1e-12, atol=0)
+    # dense A = -L on PE, with the shell coupling moved to the right-hand side
+    st = oracle.stencil_info(ws.lattice, n, 3)
+    w2 = oracle.fd2_weights(3)
+    index = {tuple(x): k for k, x in enumerate(m)}
+    A = np.zeros((npe, npe))
+    b = 4 * math.pi * rho.copy()
+    for k in range(npe):
+        for d, c in zip(st["dirs"], st["coef"]):
+            for s in range(-3, 4):
+                q = index[tuple(m[k] + s * np.asarray(d))]
+                wgt = c * w2[abs(s)]
+                if q < npe:
+                    A[k, q] -= wgt
+                else:
+                    b[k] += wgt * out["v"][q]
+    assert np.allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    v = np.linalg.solve(A, b)
+    assert np.abs(out["v"][:npe] - v).max() <= 1e-10 * np.abs(v).max()
+    assert out["e_pair"] == pytest.approx(float(rho @ v) * ws.dv, rel=1e-10)

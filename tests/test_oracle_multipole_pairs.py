@@ -177,3 +177,24 @@ def test_offsets_sets():
     # volume: the PE count approaches the sphere volume over dV
     dv = np.linalg.det(h) / np.prod(n)
     assert npe * dv == pytest.approx(4 / 3 * math.pi * 6.0 ** 3, rel=0.02)
+
+
+def test_pair_centre_rounds_half_away_from_zero():
+    """Eq. l2g's NINT: a pair midpoint that lands exactly on a half grid index
+    rounds away from zero (Fortran NINT), before the MOD.  In an 8 bohr cubic
+    cell with 8 points every quantity below is exact in binary, so the three
+    plausible rules separate: +2.5 -> 3 (round-half-even would give 2) and
+    -2.5 -> -3 = 5 mod 8 (floor(x + 0.5) and half-even would give -2 = 6)."""
+    lat = np.diag([8.0, 8.0, 8.0])
+    n = (8, 8, 8)
+    cases = [  # (C_i, C_j, expected g_ij)
+        ([2.0, 0.0, 0.0], [3.0, 0.0, 0.0], [3, 0, 0]),     # N s_mid = (2.5, 0, 0)
+        ([-3.0, 0.0, 0.0], [-2.0, 0.0, 0.0], [5, 0, 0]),   # N s_mid = (-2.5, 0, 0)
+        ([0.0, 2.0, -3.0], [0.0, 3.0, -2.0], [0, 3, 5]),   # both signs on other axes
+    ]
+    for ci, cj, g in cases:
+        rows = oracle.pair_list(lat, n, np.array([ci, cj]), 3.0)
+        r = [list(x) for x in rows if x[0] == 0 and x[1] == 1]
+        assert len(r) == 1
+        assert r[0][2:5] == [0, 0, 0]
+        assert r[0][5:8] == g, (ci, cj, r[0])
