@@ -84,6 +84,7 @@ enum { EXX_MEM_DEVICE = 0, EXX_MEM_HOST = 1 };  /* memory kind of caller buffers
  *                         (so that Tr sigma = dE_xx/dL = -E_xx/L, Eq. dexxdL).  Any
  *                         other cell returns EXX_ERR_ARG. */
 enum { EXX_STRESS_FULL = 0, EXX_STRESS_ISOTROPIC = 1, EXX_STRESS_CUBIC = 2 };
+enum { EXX_PRECOND_NONE = 0, EXX_PRECOND_MG = 1 };   /* exx_params.precond */
 
 typedef struct exx_ctx exx_ctx;
 typedef struct exx_plan exx_plan;
@@ -134,6 +135,16 @@ typedef struct {
                             /* quarter of the iterations; 0: from v = 0.  Only the starting  */
                             /* point changes: the stopping rule and the solution do not.     */
                             /* The cluster solver (exx_ctx_set_solver) ignores it.           */
+    int precond;            /* EXX_PRECOND_MG (1, default of the Python binding): the mixed  */
+                            /* path's CG is preconditioned by one multigrid V(1,1) cycle     */
+                            /* per iteration (weighted Jacobi smoothing, trilinear transfers, */
+                            /* Galerkin coarse operators built per plan on the host, the     */
+                            /* inverse of the coarsest one), which cuts the iterations by    */
+                            /* about a factor of ten.  The paper's CG is plain: only the     */
+                            /* iterates change, not the discrete equations or the stopping   */
+                            /* rule.  Used for fd_order <= 3 on the CTA solver; elsewhere,   */
+                            /* and with EXX_PRECOND_NONE (0), the CG is plain.  The FP64     */
+                            /* path is always plain CG.                                      */
 } exx_params;
 
 typedef struct {
@@ -187,7 +198,22 @@ typedef struct {
     int cluster;            /* CTAs per pair: 1 (one CTA per pair) or the cluster size of the */
                             /* cluster path, which keeps a pair's FP32 CG state in the       */
                             /* distributed shared memory of a thread-block cluster           */
+    int mg_levels;          /* multigrid levels of the non-self set (fine level included; 0: */
+                            /* no hierarchy), and their active points                        */
+    int mg_points[6];
 } exx_plan_info;
+
+/* Schedule of a plan's mixed-precision pair solver (Step IV): the knobs that
+ * change how fast the CG converges, never what it converges to (the stopping
+ * rule |b - A v| <= cg_tol |b| on the true residual is fixed).  Set from
+ * exx_params at plan creation; chosen per plan by exx_plan_autotune. */
+typedef struct {
+    int precond;            /* EXX_PRECOND_NONE or EXX_PRECOND_MG */
+    float omega;            /* weighted-Jacobi factor of the V-cycle, in (0, 1] (default 0.7) */
+    int inner_shift;        /* reliable update (double-float true residual) once the FP32    */
+                            /* residual fell by 2^-inner_shift, 4..22 (default 14)          */
+    double ms;              /* exx_plan_autotune: measured solver time of the sample, ms    */
+} exx_schedule;
 
 /* Create a context on CUDA device `device` (made current for the call). */
 int exx_ctx_create(exx_ctx **ctx, int device);
@@ -197,8 +223,17 @@ void exx_ctx_destroy(exx_ctx *ctx);
  * stencil (Eqs. nk2d_aux .. lapG_mod_nk3d, Algorithm 1) and its definiteness
  * check, proto-subdomain offset sets PE and shell for self and non-self pairs
  * (Eqs. rbar, g0), the halo check, and device workspace for up to max_orb
- * orbitals of extent box[].  Returns EXX_ERR_CELL, EXX_ERR_NK, EXX_ERR_HALO,
- * EXX_ERR_ARG or EXX_ERR_OOM on failure (and *plan = NULL). */
+ * orbitals of extent box[].  It also sizes the context's workspace for the
+ * plan -- the pair list (for all live plans of the context together, so that
+ * they can be solved as one batch), the per-cell constants and the persistent
+ * solver slots -- and, for the mixed path with EXX_PRECOND_MG, builds the
+ * multigrid hierarchy on the host.  A solve with device-memory buffers then
+ * allocates nothing, with three exceptions: the first call with EXX_MEM_HOST
+ * buffers allocates the plan's device staging copies; warm_start grows the
+ * plan's solution stores when the pair count exceeds them; and a frozen-mode
+ * cell whose auxiliary directions change rebuilds the layouts and hierarchy.
+ * Returns EXX_ERR_CELL, EXX_ERR_NK, EXX_ERR_HALO, EXX_ERR_ARG or EXX_ERR_OOM
+ * on failure (and *plan = NULL). */
 int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params,
                     int max_orb, const int box[3], exx_plan **plan);
 void exx_plan_destroy(exx_plan *plan);
@@ -219,6 +254,49 @@ int exx_pairs_solve(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const ex
  * over the cells. */
 int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, const exx_cell *cells,
                           const exx_orbitals *orbs, exx_result *res, void *stream);
+
+/* Pair sharding over ranks (one process per GPU).  The paper distributes the
+ * unique pairs over MPI processes and sums E_xx and sigma_xx over them, each
+ * process returning its D_ji contributions to the owner of orbital j (Sec.
+ * III A, Steps II and V).  After exx_plan_set_shard(plan, rank, n_ranks) the
+ * plan's solves still build the whole pair list, but solve only the pairs
+ * that exx_pair_partition assigns to `rank`; E_xx, dedh, stress, p_int and
+ * D_xx (every orbital's box) are then this rank's partial sums, whose sums
+ * over the ranks are the single-rank results (an all-reduce of 20 doubles and
+ * of the D boxes).  Per-pair outputs of other ranks' pairs are zero.  Every
+ * rank must use the same cell, orbitals and parameters.  n_ranks = 1 (the
+ * default) solves every pair.  Errors: EXX_ERR_ARG unless 0 <= rank < n_ranks. */
+int exx_plan_set_shard(exx_plan *plan, int rank, int n_ranks);
+
+/* The partition behind exx_plan_set_shard, host only (needs no GPU): the
+ * longest-processing-time rule over the pairs' estimated costs, the size N_PE
+ * of the pair's Poisson subdomain (self pairs R_PE^self, others R_PE^pair, at
+ * this cell): pairs by decreasing cost, stable, each to the least-loaded rank
+ * (the lowest on ties).  rows: host [n_pairs][8] pair rows as exx_get_pair_list
+ * returns them (only i and j are read); owner: host [n_pairs] output.
+ * Errors: EXX_ERR_ARG, and the geometry errors of exx_geometry_query. */
+int exx_pair_partition(const exx_cell *cell, const exx_params *params, int n_pairs, const int *rows, int n_ranks,
+                       int *owner);
+
+/* The plan's solver schedule (exx_schedule), and setting it by hand.
+ * set: EXX_ERR_ARG for a value out of range, or EXX_PRECOND_MG on a plan
+ * without a multigrid hierarchy (FP64 path, fd_order > 3, tiny subdomains). */
+int exx_plan_get_schedule(const exx_plan *plan, exx_schedule *sched);
+int exx_plan_set_schedule(exx_plan *plan, const exx_schedule *sched);
+
+/* Autotuner of the solver schedule (the paper has no counterpart; its CG is
+ * one fixed plain schedule).  Runs the plan's pair solver on the first
+ * `sample_pairs` pairs of this cell (the whole path up to Step IV, no D_xx)
+ * once for every candidate schedule -- the multigrid preconditioner with
+ * omega in {0.6, 0.7, 0.8}, and plain CG, each with inner_shift in {10, 14} --
+ * timing the solver launch with CUDA events on `stream`, twice per candidate
+ * (the faster run counts), and keeps the fastest for the plan's later solves
+ * (ties keep the earlier candidate, the order above).  `chosen` (may be NULL)
+ * receives it with its time.  The FP64 path has one schedule (plain FP64 CG)
+ * and returns it untimed.  cell and orb as for exx_pairs_solve (device or host
+ * memory).  Errors: those of exx_pairs_solve, EXX_ERR_ARG for sample_pairs < 1. */
+int exx_plan_autotune(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const exx_orbitals *orb, int sample_pairs,
+                      exx_schedule *chosen, void *stream);
 
 /* Copy the unique pair list of the plan's last solve to host memory: rows of
  * (i, j, k0, k1, k2, g0, g1, g2) with i <= j in lexicographic order, k the
@@ -266,6 +344,22 @@ int exx_geometry_query(const exx_cell *cell, const exx_params *params, exx_plan_
 /* Index half-widths of a D box that holds every contribution of the pairs of
  * an orbital: ceil((R_pair / 2 + R_ME) n |row alpha of h^-1|) + 1. */
 int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int halfwidth[3]);
+
+/* D-box layout of a cell (the boxes D_xx^i is written on, Step V): the extent
+ * and, per orbital, the first grid index of a box centred on the grid point
+ * nearest the orbital's centre, g_c = floor(N frac(h^-1 C) + 1/2), first index
+ * g_c - dbox / 2 (it wraps mod n like every box).
+ *   dbox:    in/out.  dbox[0] <= 0 on entry: receives the smallest extent that
+ *            holds every contribution of the orbital's pairs,
+ *            min(2 halfwidth + 1, n) with the half-widths of
+ *            exx_dbox_halfwidth; otherwise the given extent is used (for
+ *            instance one D buffer shared by the steps of a trajectory) and
+ *            must lie between that minimum and n, else EXX_ERR_ARG.
+ *   centres: host [n_orb][3] Cartesian centres (bohr), caller-owned.
+ *   dbox_lo: host [n_orb][3] output, caller-owned.
+ * Host arithmetic only: needs no GPU.  Errors: EXX_ERR_ARG, EXX_ERR_CELL. */
+int exx_dbox_layout(const exx_cell *cell, const exx_params *params, int n_orb, const double *centres, int dbox[3],
+                    int *dbox_lo);
 
 /* Strain of a cell relative to a reference cell (both lattice[alpha][a], rows
  * are lattice vectors, 9 doubles each; caller-owned host memory), the

@@ -74,7 +74,7 @@ struct exx_ctx {
     char *slots = nullptr;
     size_t slots_bytes = 0;
     SolveSlots sl_mixed{}, sl_fp64{};
-    size_t box_max = 0, npe_max = 0;
+    size_t box_max = 0, npe_max = 0, mg_max = 0;
     bool slots_dirty = false;
     // pair list
     ListDev list{};
@@ -93,6 +93,12 @@ struct exx_ctx {
     bool timing = false;
     cudaEvent_t ev[5] = {};
     double ms[4] = {};
+    // orbital rows and pairs of the live plans: the pair list is sized for all
+    // of them at plan creation, so that a solve (or a batch of the plans) finds
+    // its workspace in place
+    long long plan_rows = 0, plan_pairs = 0;
+    int sample_limit = 0;     // > 0: solve only the first pairs of the list (exx_plan_autotune)
+    int *d_perm = nullptr;    // [list capacity] pair indices of this rank's share (sharded solves)
 };
 
 struct exx_plan {
@@ -133,6 +139,11 @@ struct exx_plan {
     ClusterPart cpart[2];
     bool cl_ok[2] = {false, false};
     int32_t *d_cl_cta[2] = {}, *d_cl_rows[2] = {}, *d_cl_grc[2] = {}, *d_cl_pegl[2] = {};
+    // multigrid preconditioner of the mixed CG (params.precond), per set
+    MgDev h_mg[2] = {};               // host copy (pointers are device pointers)
+    MgDev *d_mg[2] = {};
+    std::vector<void *> mg_bufs[2];
+    bool mg_shared = false;           // self and non-self sets are the same offsets: set 1 uses set 0's tables
     int32_t *d_warm_map = nullptr;    // [max_orb][max_orb] pair index of (i, j) in d_pairs, -1 none
     float *d_warm_v[2] = {};          // solution stores; d_warm_v[warm_cur] holds the last solve's
     int warm_cap = 0;                 // pairs each store holds
@@ -140,6 +151,9 @@ struct exx_plan {
     int warm_cur = 0;
     int warm_n = 0;                   // valid pairs in d_warm_v[warm_cur]; 0: next solve starts cold
     int warm_norb = -1;
+    bool counted = false;             // rows and pairs added to the context's totals
+    exx_schedule sched{};             // solver schedule (exx_plan_set_schedule / exx_plan_autotune)
+    int shard_rank = 0, shard_n = 1;  // exx_plan_set_shard
 };
 
 static bool same_cell(const exx_cell &a, const exx_cell &b)
@@ -159,6 +173,7 @@ static int check_params(const exx_params *p)
     if (p->warm_start != 0 && p->warm_start != 1) return EXX_ERR_ARG;
     if (p->frozen < 0 || p->frozen > 2) return EXX_ERR_ARG;
     if (p->guess != 0 && p->guess != 1) return EXX_ERR_ARG;
+    if (p->precond != EXX_PRECOND_NONE && p->precond != EXX_PRECOND_MG) return EXX_ERR_ARG;
     return EXX_OK;
 }
 
@@ -173,6 +188,87 @@ static bool simple_cubic(const exx_cell &c)
             if (std::fabs(c.lattice[a][b] - want) > 1e-12 * L) return false;
         }
     return true;
+}
+
+constexpr double kMgOmega = 0.7;   // weighted-Jacobi smoothing of the multigrid V-cycle
+constexpr int kMaxBatchCells = 64;  // cells of one exx_pairs_solve_batch call
+
+static void free_mg(exx_plan *p, int s)
+{
+    for (void *b : p->mg_bufs[s]) cudaFree(b);
+    p->mg_bufs[s].clear();
+    if (p->mg_shared) {
+        // set 1 points at set 0's tables: drop that reference either way
+        p->d_mg[1] = nullptr;
+        std::memset(&p->h_mg[1], 0, sizeof(MgDev));
+        p->mg_shared = false;
+    }
+    dev_free(p->d_mg[s]);
+    std::memset(&p->h_mg[s], 0, sizeof(MgDev));
+}
+
+template <class T>
+static int mg_put(exx_plan *p, int s, const std::vector<T> &v, const T **out)
+{
+    *out = nullptr;
+    if (v.empty()) return EXX_OK;
+    T *d = nullptr;
+    int e = dev_alloc(&d, v.size());
+    if (e) return e;
+    p->mg_bufs[s].push_back(d);
+    CK(cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    *out = d;
+    return EXX_OK;
+}
+
+// The multigrid hierarchy of set s for the plan's current layout and stencil
+// (mixed precision with params.precond only; none when the set is too small
+// or the stencil reaches too far for the coarse boxes).
+static int upload_mg(exx_plan *p, int s, const SetLayout &L)
+{
+    free_mg(p, s);
+    if (p->params.precision != EXX_MIXED || p->params.precond != EXX_PRECOND_MG || p->params.fd_order > 3)
+        return EXX_OK;
+    if (s == 1 && p->off[1].m == p->off[0].m) {
+        // the same offset set (equal self and non-self radii): the same hierarchy
+        if (p->d_mg[0]) {
+            p->h_mg[1] = p->h_mg[0];
+            p->d_mg[1] = p->d_mg[0];
+            p->mg_shared = true;
+        }
+        return EXX_OK;
+    }
+    MgTables T;
+    int e = make_mg_tables(L, p->stencil, p->params.fd_order, 200, kMgOmega, T);
+    if (e) return e;
+    if (T.nlev < 2) return EXX_OK;
+    MgDev &G = p->h_mg[s];
+    std::memset(&G, 0, sizeof(G));
+    G.nlev = T.nlev;
+    G.omega = (float)kMgOmega;
+    long long off = 0;
+    for (int l = 1; l < T.nlev; ++l) {
+        MgLevelDev &v = G.lv[l];
+        v.n = T.n[l];
+        v.K = T.K[l];
+        for (int a = 0; a < 3; ++a) v.Bp[a] = T.Bp[l][a];
+        v.box = T.box[l];
+        v.stride = (T.box[l] + 63) & ~63LL;
+        v.off = off;
+        off += 3 * v.stride;
+        if ((e = mg_put(p, s, T.pts[l], &v.pts)) || (e = mg_put(p, s, T.wrow[l], &v.wrow)) ||
+            (e = mg_put(p, s, T.wexp[l], &v.wexp)) || (e = mg_put(p, s, T.dinv[l], &v.dinv)))
+            return e;
+        for (int k = 0; k < T.K[l]; ++k) {
+            G.kd[l][k] = T.kd[l][k];
+            G.wint[l][k] = T.wint[l][k];
+        }
+    }
+    G.floats = off;
+    if ((e = mg_put(p, s, T.cinv, &G.cinv))) return e;
+    if ((e = dev_alloc(&p->d_mg[s], 1))) return e;
+    CK(cudaMemcpy(p->d_mg[s], &G, sizeof(MgDev), cudaMemcpyHostToDevice));
+    return EXX_OK;
 }
 
 static void free_geometry(exx_plan *p)
@@ -193,6 +289,7 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_cl_grc[s]);
         dev_free(p->d_cl_pegl[s]);
         p->cl_ok[s] = false;
+        free_mg(p, s);
         dev_free(p->d_S64[s]);
         dev_free(p->d_T64[s]);
         dev_free(p->d_S32[s]);
@@ -252,6 +349,7 @@ static int upload_layouts(exx_plan *p)
                 CK(cudaMemcpy(p->d_cl_pegl[s], cp.pe_gl.data(), 4 * cp.pe_gl.size(), cudaMemcpyHostToDevice));
             p->cl_ok[s] = true;
         }
+        if ((e = upload_mg(p, s, L))) return e;
         p->lay[s] = std::move(L);
     }
     p->tables_valid = false;   // the shell order (halo first) may have changed
@@ -403,6 +501,9 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
     C.r_pair2 = p->params.r_pair * p->params.r_pair;
     C.stress_mode = p->params.stress_mode;
     C.guess = p->params.guess;
+    C.precond = p->sched.precond;
+    C.inner_shift = p->sched.inner_shift;
+    C.mg_omega = p->sched.omega;
     for (int s = 0; s < 2; ++s) {
         const SetLayout &L = p->lay[s];
         SetDev &S = C.set[s];
@@ -440,6 +541,7 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
         S.S32 = p->d_S32[s];
         S.T64 = p->d_T64[s];
         S.T32 = p->d_T32[s];
+        S.mg = p->d_mg[s];
     }
 }
 
@@ -474,6 +576,7 @@ static int ensure_list(exx_ctx *c, int rows, long long pairs)
     dev_free(L.cell_start);
     dev_free(L.cell_count);
     dev_free(L.total);
+    dev_free(c->d_perm);
     dev_free(L.pairs);
     dev_free(L.out);
     const int rcap = std::max(rows, 1);
@@ -481,7 +584,7 @@ static int ensure_list(exx_ctx *c, int rows, long long pairs)
     int e;
     if ((e = dev_alloc(&L.row_count, rcap)) || (e = dev_alloc(&L.row_start, rcap)) ||
         (e = dev_alloc(&L.cell_start, 64)) || (e = dev_alloc(&L.cell_count, 64)) || (e = dev_alloc(&L.total, 4)) ||
-        (e = dev_alloc(&L.pairs, pcap)) || (e = dev_alloc(&L.out, pcap)))
+        (e = dev_alloc(&L.pairs, pcap)) || (e = dev_alloc(&L.out, pcap)) || (e = dev_alloc(&c->d_perm, pcap)))
         return e;
     L.queue = L.total + 1;
     L.overflow = L.total + 2;
@@ -490,10 +593,11 @@ static int ensure_list(exx_ctx *c, int rows, long long pairs)
     return EXX_OK;
 }
 
-static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
+static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, size_t mg_max, bool mixed)
 {
     box_max = std::max(box_max, c->box_max);
     npe_max = std::max(npe_max, c->npe_max);
+    mg_max = std::max(mg_max, c->mg_max);
     const int bpm = std::max(1, solve_blocks_per_sm(mixed));
     const int n_slots = bpm * c->n_sm;
     // one layout that serves both precisions: boxes and vectors sized for doubles
@@ -521,10 +625,14 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
     o += align256(6 * kGuessBins * kNlm * 4 + 256);
     s.off_b2 = o + 128;
     o += align256(8 * npe_max + 256);
+    s.off_zf = o + 128;
+    o += align256(4 * box_max + 256);
+    s.off_mg = o + 128;
+    o += align256(4 * mg_max + 256);
     s.slot_bytes = o;
     s.n_slots = n_slots;
     const size_t need = s.slot_bytes * (size_t)n_slots;
-    if (need > c->slots_bytes || box_max > c->box_max || npe_max > c->npe_max) {
+    if (need > c->slots_bytes || box_max > c->box_max || npe_max > c->npe_max || mg_max > c->mg_max) {
         if (c->slots) cudaFree(c->slots);
         c->slots = nullptr;
         c->slots_bytes = 0;
@@ -535,6 +643,7 @@ static int ensure_slots(exx_ctx *c, size_t box_max, size_t npe_max, bool mixed)
         c->slots_bytes = need;
         c->box_max = box_max;
         c->npe_max = npe_max;
+        c->mg_max = mg_max;
         c->slots_dirty = true;
     }
     if (c->slots_dirty) {
@@ -631,6 +740,7 @@ void exx_ctx_destroy(exx_ctx *c)
     dev_free(L.total);
     dev_free(L.pairs);
     dev_free(L.out);
+    dev_free(c->d_perm);
     dev_free(c->d_cells);
     dev_free(c->d_res);
     if (c->h_cells) cudaFreeHost(c->h_cells);
@@ -657,12 +767,34 @@ int exx_plan_create(exx_ctx *ctx, const exx_cell *cell, const exx_params *params
     p->params = *params;
     p->max_orb = max_orb;
     for (int a = 0; a < 3; ++a) p->box[a] = box[a];
+    p->sched.precond = params->precond;
+    p->sched.omega = (float)kMgOmega;
+    p->sched.inner_shift = ctx->inner_shift;
     e = build_geometry(p);
+    if (!e && p->sched.precond == EXX_PRECOND_MG && !p->d_mg[0] && !p->d_mg[1])
+        p->sched.precond = EXX_PRECOND_NONE;   // no hierarchy for this plan: plain CG
     if (!e) {
         const long long pairs = (long long)max_orb * (max_orb + 1) / 2;
         p->pairs_cap = (int)std::min<long long>(pairs, 1LL << 30);
         if ((e = dev_alloc(&p->d_pairs, std::max(p->pairs_cap, 1))) ||
             (e = dev_alloc(&p->d_out, std::max(p->pairs_cap, 1))))
+            ;
+    }
+    if (!e) {
+        // the context's workspace for this plan's solves: cell constants, pair
+        // list (for every live plan together) and the persistent solver slots
+        ctx->plan_rows += max_orb;
+        ctx->plan_pairs += p->pairs_cap;
+        p->counted = true;
+        size_t box_max = 0, npe_max = 0, mg_max = 0;
+        for (int s = 0; s < 2; ++s) {
+            box_max = std::max(box_max, (size_t)p->lay[s].box);
+            npe_max = std::max(npe_max, (size_t)p->lay[s].n_pe);
+            mg_max = std::max(mg_max, (size_t)p->h_mg[s].floats);
+        }
+        if ((e = ensure_cells(ctx, kMaxBatchCells)) ||
+            (e = ensure_list(ctx, (int)std::min<long long>(ctx->plan_rows, 1LL << 30), ctx->plan_pairs)) ||
+            (e = ensure_slots(ctx, box_max, npe_max, mg_max, params->precision == EXX_MIXED)))
             ;
     }
     if (e) {
@@ -677,6 +809,10 @@ void exx_plan_destroy(exx_plan *p)
 {
     if (!p) return;
     cudaSetDevice(p->device);
+    if (p->counted) {
+        p->ctx->plan_rows -= p->max_orb;
+        p->ctx->plan_pairs -= p->pairs_cap;
+    }
     free_geometry(p);
     dev_free(p->d_phi);
     dev_free(p->d_centres);
@@ -699,6 +835,8 @@ int exx_plan_query(const exx_plan *p, exx_plan_info *info)
     info->n_me_self = p->lay[0].n_pe + p->lay[0].n_shell;
     info->n_pe_pair = p->lay[1].n_pe;
     info->n_me_pair = p->lay[1].n_pe + p->lay[1].n_shell;
+    info->mg_levels = p->h_mg[1].nlev;
+    for (int l = 0; l < p->h_mg[1].nlev && l < 6; ++l) info->mg_points[l] = l == 0 ? p->lay[1].n_pe : p->h_mg[1].lv[l].n;
     info->n_halo_self = p->lay[0].n_halo;
     info->n_halo_pair = p->lay[1].n_halo;
     info->n_aux = p->stencil.n_aux;
@@ -770,6 +908,35 @@ int exx_dbox_halfwidth(const exx_cell *cell, const exx_params *params, int hw[3]
     return EXX_OK;
 }
 
+int exx_dbox_layout(const exx_cell *cell, const exx_params *params, int n_orb, const double *centres, int dbox[3],
+                    int *dbox_lo)
+{
+    if (!cell || !params || !dbox || n_orb < 0 || (n_orb > 0 && (!centres || !dbox_lo))) return EXX_ERR_ARG;
+    int hw[3];
+    int e = exx_dbox_halfwidth(cell, params, hw);
+    if (e) return e;
+    int need[3];
+    for (int a = 0; a < 3; ++a) need[a] = std::min(2 * hw[a] + 1, cell->n[a]);
+    if (dbox[0] <= 0) {
+        for (int a = 0; a < 3; ++a) dbox[a] = need[a];
+    } else {
+        for (int a = 0; a < 3; ++a)
+            if (dbox[a] < need[a] || dbox[a] > cell->n[a]) return EXX_ERR_ARG;
+    }
+    Metric m;
+    if ((e = make_metric(cell->lattice, cell->n, m))) return e;
+    for (int i = 0; i < n_orb; ++i) {
+        const double *c = centres + 3 * (size_t)i;
+        for (int a = 0; a < 3; ++a) {
+            double f = m.hinv[a][0] * c[0] + m.hinv[a][1] * c[1] + m.hinv[a][2] * c[2];
+            f -= std::floor(f);
+            const long long g = (long long)std::floor(f * cell->n[a] + 0.5);
+            dbox_lo[3 * (size_t)i + a] = (int)(g - dbox[a] / 2);
+        }
+    }
+    return EXX_OK;
+}
+
 int exx_cell_strain(const double *lattice0, const double *lattice, double out[2])
 {
     if (!lattice0 || !lattice || !out) return EXX_ERR_ARG;
@@ -808,7 +975,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
                           const exx_orbitals *orbs, exx_result *res, void *stream_)
 {
     if (!ctx || n_cells < 1 || !plans || !cells || !orbs || !res) return EXX_ERR_ARG;
-    if (n_cells > 64) return EXX_ERR_ARG;
+    if (n_cells > kMaxBatchCells) return EXX_ERR_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     CK(cudaSetDevice(ctx->device));
     cudaGetLastError();   // clear a stale non-sticky error of an earlier unrelated call
@@ -816,6 +983,7 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     for (int c = 0; c < n_cells; ++c) {
         exx_plan *p = plans[c];
         if (!p || p->ctx != ctx || p->params.precision != prec) return EXX_ERR_ARG;
+        if (p->shard_n != plans[0]->shard_n || p->shard_rank != plans[0]->shard_rank) return EXX_ERR_ARG;
         const exx_orbitals &o = orbs[c];
         if (o.n_orb < 0 || o.n_orb > p->max_orb) return EXX_ERR_CAPACITY;
         if (o.n_orb > 0 && (!o.centres || !o.box_lo || !o.phi)) return EXX_ERR_ARG;
@@ -850,17 +1018,18 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     if (e) return e;
     int rows = 0;
     long long pairs = 0;
-    size_t box_max = 0, npe_max = 0;
+    size_t box_max = 0, npe_max = 0, mg_max = 0;
     for (int c = 0; c < n_cells; ++c) {
         rows += orbs[c].n_orb;
         pairs += (long long)orbs[c].n_orb * (orbs[c].n_orb + 1) / 2;
         for (int s = 0; s < 2; ++s) {
             box_max = std::max(box_max, (size_t)plans[c]->lay[s].box);
             npe_max = std::max(npe_max, (size_t)plans[c]->lay[s].n_pe);
+            mg_max = std::max(mg_max, (size_t)plans[c]->h_mg[s].floats);
         }
     }
     if ((e = ensure_list(ctx, rows, pairs))) return e;
-    if ((e = ensure_slots(ctx, box_max, npe_max, prec == EXX_MIXED))) return e;
+    if ((e = ensure_slots(ctx, box_max, npe_max, mg_max, prec == EXX_MIXED))) return e;
 
     // stage inputs and fill the per-cell constants (queue order)
     int row_base = 0;
@@ -951,6 +1120,31 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], stream));
     CK(launch_pair_list(ctx->d_cells, n_cells, rows, ctx->list, stream));
+    if (ctx->sample_limit > 0) CK(launch_clamp_total(ctx->list, ctx->sample_limit, stream));
+    ListDev Lsolve = ctx->list;   // the solver's view of the list (a rank's share when sharded)
+    if (plans[0]->shard_n > 1) {
+        // this rank's pairs by the LPT partition of the whole list (the same on every rank)
+        int total = 0;
+        CK(cudaMemcpyAsync(&total, ctx->list.total, 4, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        std::vector<PairRec> h_rows((size_t)std::max(total, 1));
+        if (total > 0)
+            CK(cudaMemcpy(h_rows.data(), ctx->list.pairs, sizeof(PairRec) * (size_t)total, cudaMemcpyDeviceToHost));
+        std::vector<double> cost((size_t)total);
+        for (int k = 0; k < total; ++k) {
+            const PairRec &pr = h_rows[(size_t)k];
+            cost[(size_t)k] = plans[order[pr.cell]]->lay[pr.i == pr.j ? 0 : 1].n_pe;
+        }
+        std::vector<int> owner((size_t)total), own;
+        lpt_partition(cost.data(), total, plans[0]->shard_n, owner.data());
+        for (int k = 0; k < total; ++k)
+            if (owner[(size_t)k] == plans[0]->shard_rank) own.push_back(k);
+        const int n_own = (int)own.size();
+        if (n_own) CK(cudaMemcpy(ctx->d_perm, own.data(), 4 * (size_t)n_own, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->list.total, &n_own, 4, cudaMemcpyHostToDevice));
+        if (total) CK(cudaMemsetAsync(ctx->list.out, 0, sizeof(PairOut) * (size_t)total, stream));
+        Lsolve.perm = ctx->d_perm;
+    }
     // warm start: the solution stores must hold this solve's pairs (count read back once)
     bool any_warm = false;
     for (int c = 0; c < n_cells; ++c) any_warm |= plans[c]->params.warm_start != 0;
@@ -1011,10 +1205,10 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
     }
     ctx->last_path = use_cluster ? 1 : 0;
     if (use_cluster)
-        CK(launch_solve_cluster(ctx->d_cells, ctx->list, ctx->sl_mixed, rowtab_words, cl_p, cl_g, ctx->inner_shift,
+        CK(launch_solve_cluster(ctx->d_cells, Lsolve, ctx->sl_mixed, rowtab_words, cl_p, cl_g, ctx->inner_shift,
                                 &ctx->last_clusters, stream));
     else
-        CK(launch_solve(ctx->d_cells, ctx->list, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
+        CK(launch_solve(ctx->d_cells, Lsolve, mixed ? ctx->sl_mixed : ctx->sl_fp64, mixed, ctx->inner_shift, stream));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3], stream));
     CK(launch_finalize(ctx->d_cells, n_cells, ctx->list, ctx->d_res, stream));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[4], stream));
@@ -1130,6 +1324,104 @@ int exx_pairs_solve(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const ex
     if (!plan) return EXX_ERR_ARG;
     exx_plan *plans[1] = {plan};
     return exx_pairs_solve_batch(ctx, 1, plans, cell, orb, res, stream);
+}
+
+int exx_plan_set_shard(exx_plan *plan, int rank, int n_ranks)
+{
+    if (!plan || n_ranks < 1 || rank < 0 || rank >= n_ranks) return EXX_ERR_ARG;
+    plan->shard_rank = rank;
+    plan->shard_n = n_ranks;
+    return EXX_OK;
+}
+
+int exx_pair_partition(const exx_cell *cell, const exx_params *params, int n_pairs, const int *rows, int n_ranks,
+                       int *owner)
+{
+    if (!cell || !params || n_pairs < 0 || n_ranks < 1 || (n_pairs > 0 && (!rows || !owner))) return EXX_ERR_ARG;
+    int e = check_params(params);
+    if (e) return e;
+    Metric m;
+    if ((e = make_metric(cell->lattice, cell->n, m))) return e;
+    const double rpe[2] = {params->r_pe_self, params->r_pe_pair};
+    const double rme[2] = {params->r_me_self, params->r_me_pair};
+    double npe[2];
+    for (int s = 0; s < 2; ++s) {
+        OffsetSet o;
+        if ((e = make_offsets(m, rpe[s], rme[s], o))) return e;
+        npe[s] = o.n_pe;
+    }
+    std::vector<double> cost((size_t)n_pairs);
+    for (int k = 0; k < n_pairs; ++k) cost[(size_t)k] = npe[rows[8 * (size_t)k] == rows[8 * (size_t)k + 1] ? 0 : 1];
+    lpt_partition(cost.data(), n_pairs, n_ranks, owner);
+    return EXX_OK;
+}
+
+int exx_plan_get_schedule(const exx_plan *plan, exx_schedule *sched)
+{
+    if (!plan || !sched) return EXX_ERR_ARG;
+    *sched = plan->sched;
+    return EXX_OK;
+}
+
+int exx_plan_set_schedule(exx_plan *plan, const exx_schedule *sched)
+{
+    if (!plan || !sched) return EXX_ERR_ARG;
+    if (sched->precond != EXX_PRECOND_NONE && sched->precond != EXX_PRECOND_MG) return EXX_ERR_ARG;
+    if (!(sched->omega > 0.f && sched->omega <= 1.f) || sched->inner_shift < 4 || sched->inner_shift > 22)
+        return EXX_ERR_ARG;
+    if (sched->precond == EXX_PRECOND_MG && !plan->d_mg[0] && !plan->d_mg[1]) return EXX_ERR_ARG;
+    plan->sched = *sched;
+    return EXX_OK;
+}
+
+int exx_plan_autotune(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const exx_orbitals *orb, int sample_pairs,
+                      exx_schedule *chosen, void *stream)
+{
+    if (!ctx || !plan || !cell || !orb || sample_pairs < 1 || plan->ctx != ctx) return EXX_ERR_ARG;
+    std::vector<exx_schedule> cand =
+        schedule_candidates(plan->params.precision == EXX_MIXED && (plan->d_mg[0] || plan->d_mg[1]), kMgOmega);
+    if (plan->params.precision != EXX_MIXED) {
+        plan->sched.precond = EXX_PRECOND_NONE;
+        plan->sched.ms = 0.0;
+        if (chosen) *chosen = plan->sched;
+        return EXX_OK;
+    }
+    const exx_schedule keep = plan->sched;
+    const bool timing = ctx->timing;
+    ctx->timing = true;
+    ctx->sample_limit = sample_pairs;
+    std::vector<double> ms(cand.size(), 0.0);
+    int e = EXX_OK;
+    for (size_t k = 0; k < cand.size() && !e; ++k) {
+        plan->sched = cand[k];
+        double best = 1e300;
+        for (int rep = 0; rep < 2 && !e; ++rep) {
+            exx_result r{};
+            e = exx_pairs_solve(ctx, plan, cell, orb, &r, stream);
+            if (e == EXX_ERR_CG_NOT_CONVERGED) {   // a schedule that fails the sample is never chosen
+                e = EXX_OK;
+                best = 1e300;
+                break;
+            }
+            best = std::min(best, ctx->ms[2]);
+        }
+        ms[k] = best;
+    }
+    ctx->sample_limit = 0;
+    ctx->timing = timing;
+    if (e) {
+        plan->sched = keep;
+        return e;
+    }
+    const int pick = pick_schedule(ms.data(), (int)ms.size());
+    if (pick < 0) {
+        plan->sched = keep;
+        return EXX_ERR_CG_NOT_CONVERGED;
+    }
+    plan->sched = cand[pick];
+    plan->sched.ms = ms[pick];
+    if (chosen) *chosen = plan->sched;
+    return EXX_OK;
 }
 
 }  // extern "C"

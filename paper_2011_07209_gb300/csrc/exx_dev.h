@@ -7,6 +7,38 @@ namespace exx {
 constexpr int kGuessBins = 64;   // radial bins of the multipole starting guess
 constexpr int kNlm = 49;   // (lmax + 1)^2 for lmax = 6; tables are padded to this
 
+// Multigrid preconditioner of the mixed-precision Step IV solve (V(1,1) cycle,
+// weighted Jacobi, trilinear transfers; not in the paper, whose CG is plain).
+// Level 0 is the set's dense CG box and its operator the kernel's stencil;
+// coarse levels 1 .. nlev-2 are dense boxes with a margin of kMgPadDev points,
+// each row applied over a pattern of K offsets with the level's interior
+// weights (wrow = -1) or its own weights (a row of wexp); the coarsest level
+// nlev-1 is solved with the inverse of its operator.
+constexpr int kMgLevelsDev = 6;
+constexpr int kMgKDev = 125;
+constexpr int kMgPadDev = 2;
+constexpr int kMgCoarsestDev = 256;
+struct MgLevelDev {
+    int n, K;                      // active points, pattern size
+    int Bp[3];                     // padded box
+    long long box;                 // padded box elements
+    long long off;                 // float offset of the level's R, Z, T boxes in the slot's region
+    long long stride;              // floats between R, Z and T
+    const int32_t *pts;            // [n] padded box offset of each active point
+    const int32_t *wrow;           // [n] -1 interior row, else its row in wexp
+    const float *wexp;             // [n_exp][K]
+    const float *dinv;             // [n] omega / diag(A_l)
+};
+struct MgDev {
+    int nlev;                      // levels including the fine one; 0: no hierarchy
+    float omega;                   // Jacobi weight (level 0 takes omega / diag of the stencil)
+    long long floats;              // floats of the slot region the coarse boxes need
+    MgLevelDev lv[kMgLevelsDev];   // lv[1 .. nlev-1]
+    int kd[kMgLevelsDev][kMgKDev]; // pattern offsets, (dx+2) | (dy+2) << 3 | (dz+2) << 6
+    float wint[kMgLevelsDev][kMgKDev];
+    const float *cinv;             // [n][n] inverse of the coarsest operator, row-major
+};
+
 // Geometry of one subdomain kind (self pairs or non-self pairs) of one cell.
 struct SetDev {
     int n_pe, n_shell, n_halo;
@@ -37,6 +69,7 @@ struct SetDev {
     const float *S32;
     const double *T64;             // [kNlm][n_shell] 4 pi / (2l+1) r^l Y_lm / r^(2l+1)
     const float *T32;
+    const MgDev *mg;               // multigrid hierarchy (device memory), or NULL
 };
 
 // One unique pair (i <= j): lattice image k of j and grid-resolved centre g.
@@ -77,6 +110,9 @@ struct CellDev {
     int cell_index;
     int stress_mode;               // 2: simple-cubic shortcut, the sigma integrals are skipped
     int guess;                     // 1: CG starts from the free-space multipole potential
+    int precond;                   // 1: multigrid-preconditioned mixed CG where the set has a hierarchy
+    int inner_shift;               // reliable update after the FP32 residual fell by 2^-inner_shift (0: launch default)
+    float mg_omega;                // Jacobi weight of the V-cycle (0: the tables' own)
     // warm start: initial guesses from the previous solve of the same plan
     const int32_t *warm_map;       // [n_orb][n_orb] index of pair (i, j) in warm_rows, -1 none; NULL: cold
     const PairRec *warm_rows;
@@ -125,6 +161,7 @@ struct ListDev {
     PairRec *pairs;      // [capacity]
     PairOut *out;        // [capacity]
     int capacity;
+    const int *perm;     // [*total] pair indices this launch solves (a rank's share), or NULL: 0 .. *total-1
 };
 
 }  // namespace exx

@@ -536,7 +536,7 @@ __device__ __forceinline__ F32Scale f32_scale(double sc)
 struct SlotWork {
     char *base;
     size_t slot_bytes;
-    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e, off_gs, off_b2;
+    size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e, off_gs, off_b2, off_zf, off_mg;
 };
 
 // Shared per-CTA state.
@@ -1068,6 +1068,444 @@ __device__ __forceinline__ void cg_mixed_sweep(const CgMixed &cg, int &iters, in
 }
 
 
+// ---------------------------------------------------------------------------
+// Multigrid-preconditioned mixed CG (Step IV; the paper's CG is plain, this
+// preconditioner changes the iterates only: the discrete equations of Eq. pe
+// and the stopping rule |b - A v| <= tol |b| on the true residual stay the
+// same).  FP32 preconditioned CG on A e = r in the frame of the last true
+// residual, with the same reliable updates as the plain mixed CG: when the
+// recursive residual has dropped by inner_red (or reaches the target), v += S e
+// in double-float, the double-float true residual replaces r and the PCG
+// restarts from it.  The preconditioner is one V(1,1) cycle: weighted Jacobi
+// before and after the coarse correction, trilinear prolongation P and its
+// transpose as restriction, Galerkin operators P^T A P on the coarse levels
+// (built on the host per subdomain kind) and the inverse of the coarsest one.
+// On the fine level the Jacobi weight omega / diag(A) is one constant c0 (the
+// stencil's diagonal does not vary), so the pre-smoothed residual is
+// r - c0 A r and needs no stored pre-smoothed vector.
+// ---------------------------------------------------------------------------
+struct MgSm {                      // the hierarchy of the pair's set, in shared memory
+    int nlev;
+    float c0;                      // omega / diag(A) of the fine level
+    float dscale;                  // omega / (the tables' omega): scales the coarse dinv
+    int n[kMgLevelsDev], K[kMgLevelsDev], Bp1[kMgLevelsDev], Bp2[kMgLevelsDev];
+    float *R[kMgLevelsDev], *Z[kMgLevelsDev], *T[kMgLevelsDev];
+    const int32_t *pts[kMgLevelsDev], *wrow[kMgLevelsDev];
+    const float *wexp[kMgLevelsDev], *dinv[kMgLevelsDev];
+    const float *cinv;
+    int koff[kMgLevelsDev][kMgKDev];
+    float wint[kMgLevelsDev][kMgKDev];
+    float cr[kMgCoarsestDev];
+};
+
+// L x on the four lanes of one aligned group (the stencil of stencil_group).
+template <int FDN>
+__device__ __forceinline__ void lap_group(const float *__restrict__ x_, int off, const float (*cw)[8], float center,
+                                          const int *rs, const int *dsf, const int *d2, int ndir, float (&acc)[4])
+{
+    const float4 c = ld4(x_ + off);
+    const float4 cm = ld4(x_ + off - 4);
+    const float4 cp = ld4(x_ + off + 4);
+    const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
+#pragma unroll
+    for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (d == 2 || d >= ndir) continue;
+        if (d2[d] == 0) {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_) {
+                const float4 a = ld4(x_ + off + s_ * rs[d]);
+                const float4 b = ld4(x_ + off - s_ * rs[d]);
+                acc[0] += cw[d][s_] * (a.x + b.x);
+                acc[1] += cw[d][s_] * (a.y + b.y);
+                acc[2] += cw[d][s_] * (a.z + b.z);
+                acc[3] += cw[d][s_] * (a.w + b.w);
+            }
+        } else {
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (x_[off + i + s_ * dsf[d]] + x_[off + i - s_ * dsf[d]]);
+        }
+    }
+}
+
+__device__ __forceinline__ void mg_coords(int o, int B1, int B2, int &u0, int &u1, int &u2)
+{
+    u2 = o % B2;
+    const int t = o / B2;
+    u1 = t % B1;
+    u0 = t / B1;
+}
+
+// R_{l+1} = P^T T_l on the active points of level l + 1: the values of level l
+// at 2c + delta, weights 1 (delta = 0) and 1/2 per axis.  Level 0 reads the
+// dense CG box (B1, B2, no margin), coarse levels their padded boxes.
+__device__ __forceinline__ void mg_restrict(const MgSm &m, int l, const float *__restrict__ src, int B1, int B2,
+                                            int pad)
+{
+    const int lc = l + 1;
+    const int *pts = m.pts[lc];
+    float *dst = m.R[lc];
+    for (int i = threadIdx.x; i < m.n[lc]; i += blockDim.x) {
+        const int o = pts[i];
+        int c0, c1, c2;
+        mg_coords(o, m.Bp1[lc], m.Bp2[lc], c0, c1, c2);
+        c0 -= kMgPadDev;
+        c1 -= kMgPadDev;
+        c2 -= kMgPadDev;
+        float s = 0.f;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const float *row = src + ((size_t)(2 * c0 + dx + pad) * B1 + (2 * c1 + dy + pad)) * B2 + 2 * c2 + pad;
+                const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f);
+                s += w * (row[0] + 0.5f * (row[-1] + row[1]));
+            }
+        dst[o] = s;
+    }
+}
+
+// (P Z_{l+1}) at the level-l point with unpadded coordinates (u0, u1, u2).
+__device__ __forceinline__ float mg_prolong_at(const MgSm &m, int l, int u0, int u1, int u2)
+{
+    const int lc = l + 1;
+    const float *Zc = m.Z[lc];
+    const int B1 = m.Bp1[lc], B2 = m.Bp2[lc];
+    const int a0 = u0 >> 1, a1 = u1 >> 1, a2 = u2 >> 1;
+    const int n0 = (u0 & 1) + 1, n1 = (u1 & 1) + 1;
+    const float w0 = n0 == 2 ? 0.5f : 1.f, w1 = n1 == 2 ? 0.5f : 1.f;
+    float s = 0.f;
+    for (int x = 0; x < n0; ++x)
+        for (int y = 0; y < n1; ++y) {
+            const float *row = Zc + ((size_t)(a0 + x + kMgPadDev) * B1 + (a1 + y + kMgPadDev)) * B2 + a2 + kMgPadDev;
+            s += (u2 & 1) ? 0.5f * (row[0] + row[1]) : row[0];
+        }
+    return w0 * w1 * s;
+}
+
+// y = A_l x at active point i of coarse level l (x: a padded box of level l).
+__device__ __forceinline__ float mg_apply_row(const MgSm &m, int l, int i, const float *__restrict__ x)
+{
+    const int o = m.pts[l][i];
+    const int K = m.K[l];
+    const int wr = m.wrow[l][i];
+    float s = 0.f;
+    if (wr < 0) {
+        for (int k = 0; k < K; ++k) s += m.wint[l][k] * x[o + m.koff[l][k]];
+    } else {
+        const float *w = m.wexp[l] + (size_t)wr * K;
+        for (int k = 0; k < K; ++k) s += __ldg(w + k) * x[o + m.koff[l][k]];
+    }
+    return s;
+}
+
+// Z_1 = M_1 R_1: the V(1,1) cycle on the coarse levels 1 .. nlev-1.
+__device__ __noinline__ void mg_coarse_cycle(const MgSm &m)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int L = m.nlev - 1;   // coarsest
+    // down: pre-smoothing from zero, residual, restriction
+    for (int l = 1; l < L; ++l) {
+        const int *pts = m.pts[l];
+        for (int i = tid; i < m.n[l]; i += nt) m.Z[l][pts[i]] = m.dscale * __ldg(m.dinv[l] + i) * m.R[l][pts[i]];
+        __syncthreads();
+        for (int i = tid; i < m.n[l]; i += nt) m.T[l][pts[i]] = m.R[l][pts[i]] - mg_apply_row(m, l, i, m.Z[l]);
+        __syncthreads();
+        mg_restrict(m, l, m.T[l], m.Bp1[l], m.Bp2[l], kMgPadDev);
+        __syncthreads();
+    }
+    // coarsest: z = A_L^-1 r, one warp per row
+    {
+        const int n = m.n[L];
+        float *cr = const_cast<float *>(m.cr);
+        for (int i = tid; i < n; i += nt) cr[i] = m.R[L][m.pts[L][i]];
+        __syncthreads();
+        const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+        for (int i = w; i < n; i += nw) {
+            const float *row = m.cinv + (size_t)i * n;
+            float s = 0.f;
+            for (int j = lane; j < n; j += 32) s += __ldg(row + j) * cr[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) m.Z[L][m.pts[L][i]] = s;
+        }
+        __syncthreads();
+    }
+    // up: coarse correction, post-smoothing
+    for (int l = L - 1; l >= 1; --l) {
+        const int *pts = m.pts[l];
+        for (int i = tid; i < m.n[l]; i += nt) {
+            int u0, u1, u2;
+            mg_coords(pts[i], m.Bp1[l], m.Bp2[l], u0, u1, u2);
+            m.Z[l][pts[i]] += mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
+        }
+        __syncthreads();
+        for (int i = tid; i < m.n[l]; i += nt) m.T[l][pts[i]] = m.R[l][pts[i]] - mg_apply_row(m, l, i, m.Z[l]);
+        __syncthreads();
+        for (int i = tid; i < m.n[l]; i += nt) m.Z[l][pts[i]] += m.dscale * __ldg(m.dinv[l] + i) * m.T[l][pts[i]];
+        __syncthreads();
+    }
+}
+
+// z = M r on the fine level: r in rf, z written to zout (dense boxes, zero
+// outside PE); zf holds the smoothed part z0.  Returns <r, z> (valid in warp 0).
+template <int FDN>
+__device__ __forceinline__ double mg_precondition(const CgMixed &cg, const MgSm &m, const float *__restrict__ rf,
+                                                  float *__restrict__ zf, float *__restrict__ zout)
+{
+    const SetDev &S = *cg.S;
+    const SmemCell &sm = *cg.sm;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int32_t *__restrict__ grp = S.groups;
+    const int ng = S.n_groups, ndir = cg.ndir;
+    const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
+    const float(*cw)[8] = sm.cw32;
+    const float center = sm.center32, c0 = m.c0;
+    const int B1 = S.B[1], B2 = S.B[2];
+    // pre-smoothed residual t = r - c0 A r = r + c0 L r, into zout
+    for (int g = tid; g < ng; g += nt) {
+        const int32_t gw = __ldg(grp + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        float acc[4];
+        lap_group<FDN>(rf, off, cw, center, rs, dsf, d2, ndir, acc);
+        const float4 r = ld4(rf + off);
+        st4(zout + off, (mask & 1) ? r.x + c0 * acc[0] : 0.f, (mask & 2) ? r.y + c0 * acc[1] : 0.f,
+            (mask & 4) ? r.z + c0 * acc[2] : 0.f, (mask & 8) ? r.w + c0 * acc[3] : 0.f);
+    }
+    __syncthreads();
+    mg_restrict(m, 0, zout, B1, B2, 0);
+    __syncthreads();
+    mg_coarse_cycle(m);
+    // z0 = c0 r + P Z_1 on PE
+    for (int g = tid; g < ng; g += nt) {
+        const int32_t gw = __ldg(grp + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        int u0, u1, u2;
+        mg_coords(off, B1, B2, u0, u1, u2);
+        const float4 r = ld4(rf + off);
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (mask & (1 << i)) z[i] = c0 * rv[i] + mg_prolong_at(m, 0, u0, u1, u2 + i);
+        st4(zf + off, z[0], z[1], z[2], z[3]);
+    }
+    __syncthreads();
+    // z = z0 + c0 (r - A z0) = z0 + c0 (r + L z0), and <r, z>
+    DF a[1] = {{0.f, 0.f}};
+    for (int g = tid; g < ng; g += nt) {
+        const int32_t gw = __ldg(grp + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        float acc[4];
+        lap_group<FDN>(zf, off, cw, center, rs, dsf, d2, ndir, acc);
+        const float4 r = ld4(rf + off), z0 = ld4(zf + off);
+        const float z_0 = (mask & 1) ? z0.x + c0 * (r.x + acc[0]) : 0.f;
+        const float z_1 = (mask & 2) ? z0.y + c0 * (r.y + acc[1]) : 0.f;
+        const float z_2 = (mask & 4) ? z0.z + c0 * (r.z + acc[2]) : 0.f;
+        const float z_3 = (mask & 8) ? z0.w + c0 * (r.w + acc[3]) : 0.f;
+        st4(zout + off, z_0, z_1, z_2, z_3);
+        df_add(a[0], r.x * z_0 + r.y * z_1 + r.z * z_2 + r.w * z_3);
+    }
+    block_sum_df<1>(a, reinterpret_cast<float2 *>(cg.red));
+    return (double)a[0].hi + (double)a[0].lo;
+}
+
+struct MgScalars {
+    double rz, rmax, S;
+    float alpha, beta;
+    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+};
+__shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid path
+__shared__ MgScalars g_mg_cs;
+
+// The mixed-precision solve of one pair with the multigrid preconditioner (see
+// the comment above MgSm).  zf: one more dense FP32 box; mgbase: the slot's
+// region for the coarse boxes.
+template <int FDN>
+__device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mgbase, int &iters, int &refine,
+                                         int &status, double &rnorm)
+{
+    const SetDev &S = *cg.S;
+    const SmemCell &sm = *cg.sm;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float *__restrict__ pf = cg.pf;
+    float *__restrict__ rf = cg.rf;
+    float *__restrict__ qf = cg.qf;
+    float *__restrict__ ef = cg.ef;
+    float2 *vb = reinterpret_cast<float2 *>(cg.vbox);
+    float *r32 = reinterpret_cast<float *>(cg.r64);
+    const int32_t *__restrict__ poff = S.pe_off;
+    const int32_t *__restrict__ grp = S.groups;
+    const int npe = S.n_pe, ng = S.n_groups, ndir = cg.ndir;
+    const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
+    const float(*cw)[8] = sm.cw32;
+    const float center = sm.center32;
+    const double stop = cg.stop, inner_red = cg.inner_red;
+    float2 *red2 = reinterpret_cast<float2 *>(cg.red);
+
+    MgSm &m = g_mg_sm;
+    MgScalars &cs = g_mg_cs;
+    {
+        const MgDev &G = *S.mg;
+        if (tid == 0) {
+            m.nlev = G.nlev;
+            const double om = sm.C.mg_omega > 0.f ? (double)sm.C.mg_omega : (double)G.omega;
+            m.c0 = (float)(om / -(double)sm.center64);
+            m.dscale = (float)(om / (double)G.omega);
+            m.cinv = G.cinv;
+            for (int l = 1; l < G.nlev; ++l) {
+                const MgLevelDev &v = G.lv[l];
+                m.n[l] = v.n;
+                m.K[l] = v.K;
+                m.Bp1[l] = v.Bp[1];
+                m.Bp2[l] = v.Bp[2];
+                m.R[l] = mgbase + v.off;
+                m.Z[l] = mgbase + v.off + v.stride;
+                m.T[l] = mgbase + v.off + 2 * v.stride;
+                m.pts[l] = v.pts;
+                m.wrow[l] = v.wrow;
+                m.wexp[l] = v.wexp;
+                m.dinv[l] = v.dinv;
+            }
+        }
+        for (int l = 1; l < G.nlev; ++l)
+            for (int k = tid; k < G.lv[l].K; k += nt) {
+                const int kd = G.kd[l][k];
+                const int dx = (kd & 7) - 2, dy = ((kd >> 3) & 7) - 2, dz = ((kd >> 6) & 7) - 2;
+                m.koff[l][k] = (dx * G.lv[l].Bp[1] + dy) * G.lv[l].Bp[2] + dz;
+                m.wint[l][k] = G.wint[l][k];
+            }
+        // the coarse boxes start all zero: points that are inactive for this set
+        // are read by the restriction and must hold zeros
+        for (long long k = tid; k < G.floats; k += nt) mgbase[k] = 0.f;
+        __syncthreads();
+    }
+    if (!(cg.r0n > stop)) return;   // the starting guess already meets the tolerance
+
+    // frame of the starting residual (r32 holds the last true residual in FP32)
+    double Sc = cg.r0n;
+    for (;;) {
+        {
+            const F32Scale sc = f32_scale(1.0 / Sc);
+            DF a[1] = {{0.f, 0.f}};
+            for (int k = tid; k < npe; k += nt) {
+                const int off = poff[k];
+                const float r = sc.apply(r32[k]);
+                rf[off] = r;
+                ef[off] = 0.f;
+                df_add(a[0], r * r);
+            }
+            block_sum_df<1>(a, red2);
+            if (tid == 0) cs.rmax = sqrt((double)a[0].hi + (double)a[0].lo);
+            __syncthreads();
+        }
+        const double rz0 = mg_precondition<FDN>(cg, m, rf, zf, qf);
+        if (tid == 0) {
+            cs.rz = rz0;
+            cs.S = Sc;
+        }
+        __syncthreads();
+        for (int g = tid; g < ng; g += nt) {   // p = z
+            const int off = (__ldg(grp + g) >> 4) << 2;
+            *reinterpret_cast<float4 *>(pf + off) = ld4(qf + off);
+        }
+        __syncthreads();
+        bool restart = false;
+        while (!restart) {
+            if (iters >= cg.max_iter) {
+                status = 5;
+                return;
+            }
+            // q = A p, <p, q>
+            DF a[1] = {{0.f, 0.f}};
+            for (int g = tid; g < ng; g += nt) {
+                const int32_t gw = __ldg(grp + g);
+                const int off = (gw >> 4) << 2, mask = gw & 15;
+                float acc[4];
+                lap_group<FDN>(pf, off, cw, center, rs, dsf, d2, ndir, acc);
+                const float4 p = ld4(pf + off);
+                const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
+                const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
+                st4(qf + off, q0, q1, q2, q3);
+                df_add(a[0], p.x * q0 + p.y * q1 + p.z * q2 + p.w * q3);
+            }
+            block_sum_df<1>(a, red2);
+            if (tid == 0) {
+                const double pq = (double)a[0].hi + (double)a[0].lo;
+                const double al = cs.rz / pq;
+                cs.act = (!(pq > 0.0) || !(cs.rz > 0.0) || !(al < 1e300)) ? 2 : 0;
+                cs.alpha = cs.act ? 0.f : (float)al;
+            }
+            __syncthreads();
+            const float alpha = cs.alpha;
+            int act = cs.act;
+            if (!act) {
+                // e += alpha p, r -= alpha q, <r, r>
+                DF b[1] = {{0.f, 0.f}};
+                for (int g = tid; g < ng; g += nt) {
+                    const int off = (__ldg(grp + g) >> 4) << 2;
+                    const float4 r = ld4(rf + off), q = ld4(qf + off), p = ld4(pf + off), e = ld4(ef + off);
+                    const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z,
+                                r3 = r.w - alpha * q.w;
+                    st4(rf + off, r0, r1, r2, r3);
+                    st4(ef + off, e.x + alpha * p.x, e.y + alpha * p.y, e.z + alpha * p.z, e.w + alpha * p.w);
+                    df_add(b[0], r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+                }
+                block_sum_df<1>(b, red2);
+                if (tid == 0) {
+                    const double rr = (double)b[0].hi + (double)b[0].lo;
+                    const double rn = sqrt(rr);
+                    if (!(rn == rn) || rn <= inner_red * cs.rmax || rn * cs.S <= 0.5 * stop) cs.act = 1;
+                }
+                __syncthreads();
+                act = cs.act;
+            }
+            ++iters;
+            if (act) {
+                // reliable update: v += S e in double-float, the true residual replaces r
+                ++refine;
+                const float2 S2 = dw_split(cs.S);
+                for (int k = tid; k < npe; k += nt) {
+                    const int off = poff[k];
+                    vb[off] = dw_add(vb[off], dw_mul(make_float2(ef[off], 0.f), S2));
+                    ef[off] = 0.f;
+                }
+                __syncthreads();
+                rnorm = sqrt(residual_df_n(cg.fdn, S, vb, cg.b2, r32, sm.cwdf, sm.centerdf, sm.ds, ndir, cg.red));
+                if (rnorm <= stop) return;
+                if (!(rnorm == rnorm)) {
+                    status = 5;
+                    return;
+                }
+                Sc = rnorm;
+                restart = true;
+                continue;
+            }
+            // z = M r, beta = <r, z> / <r, z>_old, p = z + beta p
+            const double rz = mg_precondition<FDN>(cg, m, rf, zf, qf);
+            if (tid == 0) {
+                cs.beta = (float)(rz / cs.rz);
+                cs.rz = rz;
+            }
+            __syncthreads();
+            const float beta = cs.beta;
+            for (int g = tid; g < ng; g += nt) {
+                const int off = (__ldg(grp + g) >> 4) << 2;
+                const float4 z = ld4(qf + off), p = ld4(pf + off);
+                st4(pf + off, z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Starting guess of the CG: the free-space potential of rho on the PE points,
 //   v(r) = sum_lm 4 pi / (2l+1) Y_lm(r^) [ r^-(l+1) q<_lm(r) + r^l q>_lm(r) ],
 // q<_lm(r) = sum_{|r'| < r} rho r'^l Y_lm dV, q>_lm(r) = sum_{|r'| > r} rho r'^-(l+1) Y_lm dV,
@@ -1291,8 +1729,9 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         __syncthreads();
         if (tid == 0) s_pair = atomicAdd(L.queue, 1);
         __syncthreads();
-        const int t = s_pair;
-        if (t >= *L.total) break;
+        const int tq = s_pair;
+        if (tq >= *L.total) break;
+        const int t = L.perm ? L.perm[tq] : tq;   // this rank's share of the list (exx_plan_set_shard)
         const PairRec pr = L.pairs[t];
         if (pr.cell != s_cell) {
             // load the cell constants into shared memory
@@ -1567,14 +2006,24 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             cg.stop = stop;
             cg.bn = bn;
             cg.r0n = rnorm;
-            cg.inner_red = inner_red;
+            cg.inner_red = C.inner_shift > 0 ? ldexp(1.0, -C.inner_shift) : inner_red;
             cg.b2 = b2;
             if (dfm) {
-                switch (fdn) {
-                case 1: cg_mixed_sweep<1>(cg, iters, refine, status, rnorm); break;
-                case 2: cg_mixed_sweep<2>(cg, iters, refine, status, rnorm); break;
-                case 3: cg_mixed_sweep<3>(cg, iters, refine, status, rnorm); break;
-                default: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
+                if (C.precond && S.mg && fdn <= 3) {
+                    float *zf = reinterpret_cast<float *>(slot + W.off_zf);
+                    float *mgb = reinterpret_cast<float *>(slot + W.off_mg);
+                    switch (fdn) {
+                    case 1: cg_mixed_mg<1>(cg, zf, mgb, iters, refine, status, rnorm); break;
+                    case 2: cg_mixed_mg<2>(cg, zf, mgb, iters, refine, status, rnorm); break;
+                    default: cg_mixed_mg<3>(cg, zf, mgb, iters, refine, status, rnorm); break;
+                    }
+                } else {
+                    switch (fdn) {
+                    case 1: cg_mixed_sweep<1>(cg, iters, refine, status, rnorm); break;
+                    case 2: cg_mixed_sweep<2>(cg, iters, refine, status, rnorm); break;
+                    case 3: cg_mixed_sweep<3>(cg, iters, refine, status, rnorm); break;
+                    default: cg_mixed_sweep<4>(cg, iters, refine, status, rnorm); break;
+                    }
                 }
                 __syncthreads();
                 // Step V integrals from the double-float solution
@@ -1684,6 +2133,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 ((float *)rv)[k] = 0.f;
                 ((float *)qv)[k] = 0.f;
                 ((float *)ev)[k] = 0.f;
+                reinterpret_cast<float *>(slot + W.off_zf)[off] = 0.f;
             }
         }
         for (int h = tid; h < S.n_halo; h += nt) vbox[S.halo_off[h]] = 0.0;
@@ -2132,8 +2582,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pair_solve_cluster(const
         cl_sync();
         if (tid == 0) s_t = cl_ldi(cl_map(smem_u32(&s_pair), 0));
         __syncthreads();
-        const int t = s_t;
-        if (t >= *L.total) break;
+        const int tq = s_t;
+        if (tq >= *L.total) break;
+        const int t = L.perm ? L.perm[tq] : tq;
         const PairRec pr = L.pairs[t];
         const int self = (pr.i == pr.j);
         if (pr.cell != s_cell) {
@@ -2558,6 +3009,8 @@ cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlot
     W.off_e = slots.off_e;
     W.off_gs = slots.off_gs;
     W.off_b2 = slots.off_b2;
+    W.off_zf = slots.off_zf;
+    W.off_mg = slots.off_mg;
     if (mixed) k_pair_solve<float><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     else k_pair_solve<double><<<slots.n_slots, kSolveThreads, 0, s>>>(cells, L, W, inner_shift);
     return cudaGetLastError();
@@ -2577,6 +3030,17 @@ cudaError_t launch_warm_map(const PairRec *rows, int n, int n_orb, int *map, cud
 {
     if (n <= 0) return cudaSuccess;
     k_warm_map<<<(n + 255) / 256, 256, 0, s>>>(rows, n, n_orb, map);
+    return cudaGetLastError();
+}
+
+// Limit the solver's queue to the first `limit` pairs (schedule autotuning).
+__global__ void k_clamp_total(ListDev L, int limit)
+{
+    if (threadIdx.x == 0 && *L.total > limit) *L.total = limit;
+}
+cudaError_t launch_clamp_total(const ListDev &L, int limit, cudaStream_t s)
+{
+    k_clamp_total<<<1, 32, 0, s>>>(L, limit);
     return cudaGetLastError();
 }
 

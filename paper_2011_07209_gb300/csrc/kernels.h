@@ -23,6 +23,8 @@ struct SolveSlots {
     size_t off_vbox, off_pbox, off_rho, off_r64, off_r, off_q, off_e;
     size_t off_gs;   // 6 kGuessBins kNlm floats: binned moments of the starting guess
     size_t off_b2;   // n_pe float pairs: 4 pi rho as hi + lo (double-float residuals)
+    size_t off_zf;   // dense FP32 box: the smoothed part z0 of the preconditioned residual (multigrid)
+    size_t off_mg;   // coarse-level boxes of the multigrid preconditioner
     int n_slots;
 };
 
@@ -33,6 +35,7 @@ cudaError_t launch_gather_rows(const float *src, const int32_t *perm, int n, flo
 cudaError_t launch_pair_list(const CellDev *cells, int n_cells, int n_rows, const ListDev &L, cudaStream_t s);
 cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlots &slots, bool mixed,
                          int inner_shift, cudaStream_t s);
+cudaError_t launch_clamp_total(const ListDev &L, int limit, cudaStream_t s);
 cudaError_t launch_finalize(const CellDev *cells, int n_cells, const ListDev &L, CellResult *res, cudaStream_t s);
 int solve_blocks_per_sm(bool mixed);
 

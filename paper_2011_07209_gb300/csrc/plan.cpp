@@ -752,5 +752,164 @@ int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
     return EXX_OK;
 }
 
-}  // namespace exx
+// Device form of the hierarchy (see plan.h).
+int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t)
+{
+    t = MgTables();
+    std::vector<MgLevel> lv;
+    int e = make_mg_levels(L, st, fd_n, min_points, lv);
+    if (e) return e;
+    const int nl = (int)lv.size();
+    if (nl < 2 || nl > kMgMaxLevels || lv.back().n > kMgMaxCoarsest) return EXX_OK;   // no hierarchy
+    auto coords = [](const int *B, long long o, int *u) {
+        u[2] = (int)(o % B[2]);
+        u[1] = (int)((o / B[2]) % B[1]);
+        u[0] = (int)(o / ((long long)B[1] * B[2]));
+    };
+    MgTables r;
+    r.nlev = nl;
+    r.n[0] = lv[0].n;
+    for (int l = 1; l < nl; ++l) {
+        const MgLevel &A = lv[l];
+        r.n[l] = A.n;
+        for (int a = 0; a < 3; ++a) r.Bp[l][a] = A.B[a] + 2 * kMgPad;
+        r.box[l] = (long long)r.Bp[l][0] * r.Bp[l][1] * r.Bp[l][2];
+        r.slot_floats += 3 * ((r.box[l] + 63) & ~63LL);
+        std::vector<int> u((size_t)3 * A.n);
+        r.pts[l].resize(A.n);
+        for (int i = 0; i < A.n; ++i) {
+            coords(A.B, A.pts[i], &u[3 * (size_t)i]);
+            const int *v = &u[3 * (size_t)i];
+            r.pts[l][i] = (int32_t)((((long long)v[0] + kMgPad) * r.Bp[l][1] + v[1] + kMgPad) * r.Bp[l][2] + v[2] +
+                                    kMgPad);
+        }
+        if (l == nl - 1) {
+            // coarsest: the inverse of A_l by Gauss-Jordan elimination (SPD, no pivoting needed)
+            const int n = A.n;
+            std::vector<double> a((size_t)n * n, 0.0), inv((size_t)n * n, 0.0);
+            for (int i = 0; i < n; ++i) {
+                inv[(size_t)i * n + i] = 1.0;
+                for (int k = A.row[i]; k < A.row[i + 1]; ++k) a[(size_t)i * n + A.col[k]] = A.val[k];
+            }
+            for (int c = 0; c < n; ++c) {
+                const double piv = a[(size_t)c * n + c];
+                if (!(piv > 0.0)) return EXX_OK;
+                for (int k = 0; k < n; ++k) {
+                    a[(size_t)c * n + k] /= piv;
+                    inv[(size_t)c * n + k] /= piv;
+                }
+                for (int i = 0; i < n; ++i) {
+                    if (i == c) continue;
+                    const double f = a[(size_t)i * n + c];
+                    if (f == 0.0) continue;
+                    for (int k = 0; k < n; ++k) {
+                        a[(size_t)i * n + k] -= f * a[(size_t)c * n + k];
+                        inv[(size_t)i * n + k] -= f * inv[(size_t)c * n + k];
+                    }
+                }
+            }
+            r.cinv.resize((size_t)n * n);
+            for (size_t k = 0; k < r.cinv.size(); ++k) r.cinv[k] = (float)inv[k];
+            continue;
+        }
+        // interior stencil: the row of the active point nearest the centre of the set
+        double cm[3] = {0, 0, 0};
+        for (int i = 0; i < A.n; ++i)
+            for (int a = 0; a < 3; ++a) cm[a] += u[3 * (size_t)i + a];
+        for (int a = 0; a < 3; ++a) cm[a] /= A.n;
+        int i0 = 0;
+        double best = 1e300;
+        for (int i = 0; i < A.n; ++i) {
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) d2 += (u[3 * (size_t)i + a] - cm[a]) * (u[3 * (size_t)i + a] - cm[a]);
+            if (d2 < best) {
+                best = d2;
+                i0 = i;
+            }
+        }
+        int pidx[125];
+        std::fill(pidx, pidx + 125, -1);
+        int K = 0;
+        std::vector<double> wint;
+        auto key = [&](int i, int j, int *d) {
+            for (int a = 0; a < 3; ++a) d[a] = u[3 * (size_t)j + a] - u[3 * (size_t)i + a];
+            if (std::abs(d[0]) > kMgPad || std::abs(d[1]) > kMgPad || std::abs(d[2]) > kMgPad) return -1;
+            return ((d[0] + 2) * 5 + d[1] + 2) * 5 + d[2] + 2;
+        };
+        for (int k = A.row[i0]; k < A.row[i0 + 1]; ++k) {
+            int d[3];
+            const int kk = key(i0, A.col[k], d);
+            if (kk < 0 || K >= kMgMaxK) return EXX_OK;
+            pidx[kk] = K;
+            r.kd[l][K] = (d[0] + 2) | (d[1] + 2) << 3 | (d[2] + 2) << 6;
+            r.wint[l][K] = (float)A.val[k];
+            wint.push_back(A.val[k]);
+            ++K;
+        }
+        r.K[l] = K;
+        r.wrow[l].assign(A.n, -1);
+        r.dinv[l].resize(A.n);
+        std::vector<double> w(K);
+        for (int i = 0; i < A.n; ++i) {
+            std::fill(w.begin(), w.end(), 0.0);
+            bool same = (A.row[i + 1] - A.row[i]) == K;
+            double diag = 0.0;
+            for (int k = A.row[i]; k < A.row[i + 1]; ++k) {
+                int d[3];
+                const int kk = key(i, A.col[k], d);
+                if (kk < 0 || pidx[kk] < 0) return EXX_OK;   // an entry outside the interior pattern
+                w[pidx[kk]] = A.val[k];
+                if (A.col[k] == i) diag = A.val[k];
+            }
+            if (!(diag > 0.0)) return EXX_OK;
+            r.dinv[l][i] = (float)(omega / diag);
+            for (int k = 0; k < K && same; ++k)
+                same = std::fabs(w[k] - wint[k]) <= 1e-12 * std::fabs(wint[k]);
+            if (same) continue;
+            r.wrow[l][i] = r.n_exp[l]++;
+            for (int k = 0; k < K; ++k) r.wexp[l].push_back((float)w[k]);
+        }
+    }
+    t = std::move(r);
+    return EXX_OK;
+}
 
+int pick_schedule(const double *ms, int n)
+{
+    int best = -1;
+    for (int k = 0; k < n; ++k)
+        if (std::isfinite(ms[k]) && ms[k] < 1e299 && (best < 0 || ms[k] < ms[best])) best = k;
+    return best;
+}
+
+std::vector<exx_schedule> schedule_candidates(bool mg, double omega_default)
+{
+    std::vector<exx_schedule> c;
+    if (mg)
+        for (float om : {0.7f, 0.6f, 0.8f})
+            for (int sh : {14, 10}) c.push_back({EXX_PRECOND_MG, om, sh, 0.0});
+    for (int sh : {14, 10}) c.push_back({EXX_PRECOND_NONE, (float)omega_default, sh, 0.0});
+    return c;
+}
+
+void lpt_partition(const double *cost, int n, int n_ranks, int *owner)
+{
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // min-heap of (load, rank): the least loaded rank, the lowest on ties
+    std::vector<std::pair<double, int>> heap;
+    for (int r = 0; r < n_ranks; ++r) heap.push_back({0.0, r});
+    auto greater = [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first || (a.first == b.first && a.second > b.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), greater);
+    for (int k : order) {
+        std::pop_heap(heap.begin(), heap.end(), greater);
+        owner[k] = heap.back().second;
+        heap.back().first += cost[k];
+        std::push_heap(heap.begin(), heap.end(), greater);
+    }
+}
+
+}  // namespace exx

@@ -8,6 +8,8 @@
 #include <cstdint>
 #include <vector>
 
+#include "../../include/exx.h"
+
 namespace exx {
 
 constexpr int kMaxFd = 6;     // largest stencil half-width n
@@ -96,6 +98,52 @@ struct MgLevel {
 };
 // Levels until one has at most min_points points (that one included).
 int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_points, std::vector<MgLevel> &lv);
+
+// The hierarchy in the form the pair solver applies it (V(1,1) cycle, weighted
+// Jacobi smoothing, trilinear transfers).  Level 0 is the dense CG box itself,
+// whose operator is the kernel's own stencil.  Coarse levels 1 .. nlev-2 are
+// dense boxes with a margin of kMgPad points on every side (coordinate u of
+// level l sits at u + kMgPad), each row of A_l applied over one pattern of K
+// offsets: rows equal to the level's interior stencil (the row of the most
+// central point) take the shared weights wint, the others (rows that the
+// Dirichlet boundary of the subdomain truncates) their own K weights in wexp,
+// zero where the row has no entry.  dinv = omega / diag(A_l).  The coarsest
+// level nlev-1 is solved exactly with the inverse of its operator (cinv,
+// row-major over its active points).  Every operator is FP32.
+constexpr int kMgPad = 2;          // margin of the coarse boxes (the coarse stencil reach)
+constexpr int kMgMaxLevels = 6;    // fine level included
+constexpr int kMgMaxK = 125;       // 5 x 5 x 5 pattern positions
+constexpr int kMgMaxCoarsest = 256;
+struct MgTables {
+    int nlev = 0;                                   // 0: no hierarchy (too small, or a reach above kMgPad)
+    int n[kMgMaxLevels] = {};                       // active points per level
+    int Bp[kMgMaxLevels][3] = {};                   // padded boxes of the coarse levels
+    long long box[kMgMaxLevels] = {};               // their sizes
+    int K[kMgMaxLevels] = {};
+    int kd[kMgMaxLevels][kMgMaxK] = {};             // pattern offsets (dx+2) | (dy+2) << 3 | (dz+2) << 6
+    float wint[kMgMaxLevels][kMgMaxK] = {};
+    int n_exp[kMgMaxLevels] = {};
+    std::vector<int32_t> pts[kMgMaxLevels];         // padded box offset of each active point
+    std::vector<int32_t> wrow[kMgMaxLevels];        // -1: interior row, else its row in wexp
+    std::vector<float> wexp[kMgMaxLevels];          // [n_exp][K]
+    std::vector<float> dinv[kMgMaxLevels];
+    std::vector<float> cinv;                        // [n][n] of the coarsest level
+    long long slot_floats = 0;                      // three boxes per coarse level
+};
+int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t);
+
+// Candidate schedules of the autotuner (exx_plan_autotune), in the order that
+// breaks ties: with a multigrid hierarchy, MG with omega 0.7, 0.6, 0.8, each
+// with inner_shift 14 then 10; then plain CG with inner_shift 14, 10.
+std::vector<exx_schedule> schedule_candidates(bool mg, double omega_default);
+// Longest-processing-time partition of n jobs over n_ranks: jobs in order of
+// decreasing cost (equal costs keep their order), each given to the rank with
+// the least load so far (the lowest rank on ties).  owner[k] receives job k's rank.
+void lpt_partition(const double *cost, int n, int n_ranks, int *owner);
+
+// The autotuner's choice among n measured candidates: the index of the
+// smallest finite time, the first on ties; -1 when none is finite.
+int pick_schedule(const double *ms, int n);
 
 // Row partition of one set over a cluster of nc CTAs (the cluster CG path).
 // The box rows (plane z, row y) that hold PE or halo points are taken in

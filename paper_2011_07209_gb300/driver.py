@@ -113,3 +113,31 @@ def run_batch(ctx: exx.Context, runs, *, pair_outputs=False, stream=None, check=
     for o in outs:
         o["status"] = code
     return outs
+
+
+def reduce_shards(out: dict, dxx, dist) -> dict:
+    """Sum a sharded solve's partial results over the ranks of `dist` (a
+    torch.distributed module with an initialised process group): E_xx, dE/dh,
+    Pi_xx and p_int (one all-reduce of 20 doubles) and the D_xx boxes (one
+    all-reduce of the D buffer, when given).  The sums are the single-rank
+    results (Sec. III A, Step V: MPI_SUM of E_xx and sigma, D_ji returned to
+    the owner of orbital j).  Returns a copy of `out` with the summed scalars."""
+    import torch
+    dev = dxx.device if dxx is not None else torch.device("cpu")
+    if dev.type == "cpu" or dist.get_backend() == "gloo":
+        dev_s = torch.device("cpu")
+    else:
+        dev_s = dev
+    v = torch.tensor([out["e_xx"], *np.asarray(out["dedh"], float).ravel(), *np.asarray(out["stress"], float).ravel(),
+                      out["p_int"]], dtype=torch.float64, device=dev_s)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    if dxx is not None:
+        dist.all_reduce(dxx, op=dist.ReduceOp.SUM)
+    v = v.cpu().numpy()
+    red = dict(out)
+    red["e_xx"] = float(v[0])
+    red["dedh"] = v[1:10].reshape(3, 3)
+    red["stress"] = v[10:19].reshape(3, 3)
+    red["p_int"] = float(v[19])
+    return red
+

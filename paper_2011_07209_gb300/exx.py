@@ -20,6 +20,7 @@ OK, ERR_ARG, ERR_CELL, ERR_HALO, ERR_NK, ERR_CG, ERR_CAPACITY, ERR_BOX, ERR_OOM,
 FP64, MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 STRESS_FULL, STRESS_ISOTROPIC, STRESS_CUBIC = 0, 1, 2
+PRECOND_NONE, PRECOND_MG = 0, 1
 SOLVER_CTA, SOLVER_CLUSTER = 0, 1
 
 _lib = None
@@ -28,7 +29,9 @@ _lock = threading.Lock()
 EXPORTS = ("exx_ctx_create", "exx_ctx_destroy", "exx_plan_create", "exx_plan_destroy", "exx_plan_query",
            "exx_pairs_solve", "exx_pairs_solve_batch", "exx_get_pair_list", "exx_dbox_halfwidth",
            "exx_ctx_set_timing", "exx_ctx_get_timing", "exx_error_string", "exx_last_error_detail", "exx_version",
-           "exx_pair_list_noalloc", "exx_ctx_set_solver", "exx_cell_strain", "exx_geometry_query")
+           "exx_pair_list_noalloc", "exx_ctx_set_solver", "exx_cell_strain", "exx_geometry_query",
+           "exx_dbox_layout", "exx_plan_get_schedule", "exx_plan_set_schedule", "exx_plan_autotune",
+           "exx_plan_set_shard", "exx_pair_partition")
 
 
 class Cell(C.Structure):
@@ -40,7 +43,7 @@ class Params(C.Structure):
                 ("r_me_self", C.c_double), ("r_me_pair", C.c_double), ("cg_tol", C.c_double),
                 ("fd_order", C.c_int), ("lmax", C.c_int), ("cg_max_iter", C.c_int), ("nq", C.c_int),
                 ("precision", C.c_int), ("frozen", C.c_int), ("stress_mode", C.c_int), ("warm_start", C.c_int),
-                ("guess", C.c_int)]
+                ("guess", C.c_int), ("precond", C.c_int)]
 
 
 class Orbitals(C.Structure):
@@ -57,12 +60,22 @@ class Result(C.Structure):
                 ("total_refine", C.c_longlong), ("p_int", C.c_double), ("n_warm", C.c_int)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("precond", C.c_int), ("omega", C.c_float), ("inner_shift", C.c_int), ("ms", C.c_double)]
+
+
+def schedule_dict(sc: Schedule) -> dict:
+    return {"precond": "mg" if sc.precond == PRECOND_MG else "none", "omega": round(float(sc.omega), 4),
+            "inner_shift": int(sc.inner_shift), "ms": float(sc.ms)}
+
+
 class PlanInfo(C.Structure):
     _fields_ = [("n_pe_self", C.c_int), ("n_me_self", C.c_int), ("n_pe_pair", C.c_int), ("n_me_pair", C.c_int),
                 ("n_halo_self", C.c_int), ("n_halo_pair", C.c_int), ("n_aux", C.c_int), ("n_stcl", C.c_int),
                 ("dirs", C.c_int * 18), ("coef", C.c_double * 6), ("aux_frozen", C.c_int * 9),
                 ("box_self", C.c_int * 3), ("box_pair", C.c_int * 3), ("workspace_bytes", C.c_longlong),
-                ("pair_capacity", C.c_int), ("ctas", C.c_int), ("threads", C.c_int), ("cluster", C.c_int)]
+                ("pair_capacity", C.c_int), ("ctas", C.c_int), ("threads", C.c_int), ("cluster", C.c_int),
+                ("mg_levels", C.c_int), ("mg_points", C.c_int * 6)]
 
 
 class ExxError(RuntimeError):
@@ -108,6 +121,15 @@ def lib(build_if_missing: bool = False):
             L.exx_dbox_halfwidth.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(C.c_int)]
             L.exx_cell_strain.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.exx_geometry_query.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.POINTER(PlanInfo)]
+            L.exx_dbox_layout.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.c_int, C.c_void_p,
+                                          C.POINTER(C.c_int), C.c_void_p]
+            L.exx_plan_set_shard.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.exx_pair_partition.argtypes = [C.POINTER(Cell), C.POINTER(Params), C.c_int, C.c_void_p, C.c_int,
+                                             C.c_void_p]
+            L.exx_plan_get_schedule.argtypes = [C.c_void_p, C.POINTER(Schedule)]
+            L.exx_plan_set_schedule.argtypes = [C.c_void_p, C.POINTER(Schedule)]
+            L.exx_plan_autotune.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(Cell), C.POINTER(Orbitals), C.c_int,
+                                            C.POINTER(Schedule), C.c_void_p]
             L.exx_ctx_set_timing.argtypes = [C.c_void_p, C.c_int]
             L.exx_ctx_set_solver.argtypes = [C.c_void_p, C.c_int]
             L.exx_pair_list_noalloc.argtypes = [C.POINTER(Cell), C.c_void_p, C.c_int, C.c_double, C.c_int,
@@ -133,7 +155,7 @@ def make_cell(lattice, n) -> Cell:
 
 def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, tol=1e-9, fd_order=3, lmax=6,
                 max_iter=20000, nq=15, precision=MIXED, frozen=False, stress_mode=0, warm_start=False,
-                guess=True) -> Params:
+                guess=True, precond=PRECOND_MG) -> Params:
     p = Params()
     p.r_pair = r_pair
     p.r_pe_pair = r_pe
@@ -150,6 +172,7 @@ def make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, r_pe_self=None, r_me_self=None, 
     p.stress_mode = int(stress_mode)
     p.warm_start = int(bool(warm_start))
     p.guess = int(bool(guess))
+    p.precond = int(precond)
     return p
 
 
@@ -191,25 +214,31 @@ class Reassembly:
         return self.eps_max is not None and cell_strain(lattice0, lattice)[0] > self.eps_max
 
 
-def dbox_layout(lattice, n, centres, params: Params, dbox=None):
-    """D-box extent and per-orbital first index (box around each centre's grid point).
+def pair_partition(lattice, n, params: Params, rows, n_ranks: int) -> np.ndarray:
+    """exx_pair_partition: the rank of every pair row (host arithmetic, no GPU)."""
+    rows = np.ascontiguousarray(np.asarray(rows, np.int32).reshape(-1, 8))
+    owner = np.zeros(rows.shape[0], np.int32)
+    _check(lib().exx_pair_partition(C.byref(make_cell(lattice, n)), C.byref(params), rows.shape[0],
+                                    rows.ctypes.data_as(C.c_void_p), int(n_ranks), owner.ctypes.data_as(C.c_void_p)),
+           "exx_pair_partition")
+    return owner
 
-    A caller-chosen dbox (at least the required extent) can be given, e.g. to
-    share one D buffer between the steps of a trajectory."""
-    n = np.asarray(n, np.int64)
-    hw = dbox_halfwidth(lattice, n, params)
-    need = np.minimum(2 * hw + 1, n)
-    if dbox is None:
-        dbox = need
-    else:
-        dbox = np.asarray(dbox, np.int64)
-        if np.any(dbox < need) or np.any(dbox > n):
-            raise ValueError(f"dbox {dbox} outside [{need}, {n}]")
-    hinv = np.linalg.inv(np.asarray(lattice, float).T)
-    frac = np.asarray(centres, float) @ hinv.T
-    frac -= np.floor(frac)
-    gc = np.floor(frac * n + 0.5).astype(np.int64)
-    return dbox.astype(np.int32), (gc - dbox // 2).astype(np.int32)
+
+def dbox_layout(lattice, n, centres, params: Params, dbox=None):
+    """exx_dbox_layout: D-box extent and per-orbital first index (box around
+    each centre's grid point).  A caller-chosen dbox (at least the required
+    extent) can be given, e.g. to share one D buffer between the steps of a
+    trajectory."""
+    cen = np.ascontiguousarray(np.asarray(centres, float).reshape(-1, 3))
+    n_orb = cen.shape[0]
+    db = (C.c_int * 3)(*([0, 0, 0] if dbox is None else [int(x) for x in dbox]))
+    lo = np.zeros((n_orb, 3), np.int32)
+    code = lib().exx_dbox_layout(C.byref(make_cell(lattice, n)), C.byref(params), n_orb,
+                                 cen.ctypes.data_as(C.c_void_p), db, lo.ctypes.data_as(C.c_void_p))
+    if code == ERR_ARG and dbox is not None:
+        raise ValueError(f"dbox {list(dbox)} outside the allowed range for this cell")
+    _check(code, "exx_dbox_layout")
+    return np.array(list(db), np.int32), lo
 
 
 class Context:
@@ -255,6 +284,7 @@ def _info_dict(pi: PlanInfo) -> dict:
         "aux": np.array(list(pi.aux_frozen)).reshape(3, 3)[:pi.n_aux],
         "box_self": list(pi.box_self), "box_pair": list(pi.box_pair), "workspace_bytes": pi.workspace_bytes,
         "pair_capacity": pi.pair_capacity, "ctas": pi.ctas, "threads": pi.threads, "cluster": pi.cluster,
+        "mg_points": list(pi.mg_points)[:pi.mg_levels],
     }
 
 
@@ -281,6 +311,27 @@ class Plan:
         pi = PlanInfo()
         _check(lib().exx_plan_query(self.handle, C.byref(pi)), "exx_plan_query")
         return _info_dict(pi)
+
+    def set_shard(self, rank: int, n_ranks: int):
+        """Solve only this rank's share of the pairs (exx_plan_set_shard); results are partial sums."""
+        _check(lib().exx_plan_set_shard(self.handle, int(rank), int(n_ranks)), "exx_plan_set_shard")
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(lib().exx_plan_get_schedule(self.handle, C.byref(sc)), "exx_plan_get_schedule")
+        return schedule_dict(sc)
+
+    def set_schedule(self, precond, omega=0.7, inner_shift=14):
+        sc = Schedule(int(precond), float(omega), int(inner_shift), 0.0)
+        _check(lib().exx_plan_set_schedule(self.handle, C.byref(sc)), "exx_plan_set_schedule")
+
+    def autotune(self, ctx, lattice, n, orb, sample_pairs=304, stream=None) -> dict:
+        """exx_plan_autotune on this cell's first `sample_pairs` pairs; returns the chosen schedule."""
+        sc = Schedule()
+        s = C.c_void_p(stream) if isinstance(stream, int) else stream
+        _check(lib().exx_plan_autotune(ctx.handle, self.handle, C.byref(make_cell(lattice, n)), C.byref(orb),
+                                       int(sample_pairs), C.byref(sc), s), "exx_plan_autotune")
+        return schedule_dict(sc)
 
     def pair_list(self) -> np.ndarray:
         n = C.c_int()

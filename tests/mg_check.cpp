@@ -103,6 +103,7 @@ struct Mg {
             x[i] /= chol[(size_t)i * nc + i];
         }
     }
+    void apply_pre(const Vec &r, Vec &z) const { vcycle(0, r, z); }
     void vcycle(size_t l, const Vec &r, Vec &x) const
     {
         if (l + 1 == lv.size()) {
@@ -128,12 +129,156 @@ struct Mg {
     }
 };
 
-static int pcg(const MgLevel &A, const Vec &b, const Mg *M, double tol, Vec &x)
+// The same V(1,1) cycle computed from the device tables (make_mg_tables), in
+// FP32 on padded dense boxes, the way the pair solver applies it: level 0 is
+// the CSR fine operator on the fine box, coarse rows take the interior stencil
+// or their explicit weights, the coarsest level its inverse.
+struct MgT {
+    const MgTables *T;
+    const MgLevel *fine;       // level 0 (box and active points)
+    float c0;                  // omega / diag of the fine operator
+
+    static void unpack(int kd, int *d)
+    {
+        d[0] = (kd & 7) - 2;
+        d[1] = ((kd >> 3) & 7) - 2;
+        d[2] = ((kd >> 6) & 7) - 2;
+    }
+    // y = A_l x on the active points of coarse level l (boxes)
+    void apply(int l, const std::vector<float> &x, std::vector<float> &y) const
+    {
+        const MgTables &t = *T;
+        y.assign(t.box[l], 0.f);
+        for (int i = 0; i < t.n[l]; ++i) {
+            const int o = t.pts[l][i];
+            const float *w = t.wrow[l][i] < 0 ? t.wint[l] : &t.wexp[l][(size_t)t.wrow[l][i] * t.K[l]];
+            float s = 0.f;
+            for (int k = 0; k < t.K[l]; ++k) {
+                int d[3];
+                unpack(t.kd[l][k], d);
+                s += w[k] * x[o + (d[0] * t.Bp[l][1] + d[1]) * t.Bp[l][2] + d[2]];
+            }
+            y[o] = s;
+        }
+    }
+    // coordinates of level l's box element o (without the margin), and the inverse
+    void coords(int l, long long o, int *u) const
+    {
+        const int *B = l == 0 ? fine->B : T->Bp[l];
+        u[2] = (int)(o % B[2]);
+        u[1] = (int)((o / B[2]) % B[1]);
+        u[0] = (int)(o / ((long long)B[1] * B[2]));
+        if (l > 0)
+            for (int a = 0; a < 3; ++a) u[a] -= kMgPad;
+    }
+    long long offset(int l, const int *u) const
+    {
+        const int *B = l == 0 ? fine->B : T->Bp[l];
+        const int p = l == 0 ? 0 : kMgPad;
+        return (((long long)u[0] + p) * B[1] + u[1] + p) * B[2] + u[2] + p;
+    }
+    // coarse point c of level l+1 gathers level-l box values at 2c + delta
+    void restrict_to(int l, const std::vector<float> &fb, std::vector<float> &cb) const
+    {
+        cb.assign(T->box[l + 1], 0.f);
+        for (int i = 0; i < T->n[l + 1]; ++i) {
+            int c[3];
+            coords(l + 1, T->pts[l + 1][i], c);
+            float s = 0.f;
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int u[3] = {2 * c[0] + dx, 2 * c[1] + dy, 2 * c[2] + dz};
+                        const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
+                        s += w * fb[offset(l, u)];
+                    }
+            cb[T->pts[l + 1][i]] = s;
+        }
+    }
+    // value of the prolongation of level l+1's box at level-l point u
+    float prolong_at(int l, const std::vector<float> &cb, const int *u) const
+    {
+        int cc[3][2], np[3];
+        float ww[3][2];
+        for (int a = 0; a < 3; ++a) {
+            cc[a][0] = u[a] >> 1;
+            if (u[a] & 1) {
+                cc[a][1] = (u[a] >> 1) + 1;
+                ww[a][0] = ww[a][1] = 0.5f;
+                np[a] = 2;
+            } else {
+                ww[a][0] = 1.f;
+                np[a] = 1;
+            }
+        }
+        float s = 0.f;
+        for (int x = 0; x < np[0]; ++x)
+            for (int y = 0; y < np[1]; ++y)
+                for (int z = 0; z < np[2]; ++z) {
+                    const int c[3] = {cc[0][x], cc[1][y], cc[2][z]};
+                    s += ww[0][x] * ww[1][y] * ww[2][z] * cb[offset(l + 1, c)];
+                }
+        return s;
+    }
+    // z_l = M_l r_l on coarse level l (boxes)
+    void cycle(int l, const std::vector<float> &r, std::vector<float> &z) const
+    {
+        const MgTables &t = *T;
+        z.assign(t.box[l], 0.f);
+        if (l == t.nlev - 1) {
+            const int n = t.n[l];
+            for (int i = 0; i < n; ++i) {
+                float s = 0.f;
+                for (int j = 0; j < n; ++j) s += t.cinv[(size_t)i * n + j] * r[t.pts[l][j]];
+                z[t.pts[l][i]] = s;
+            }
+            return;
+        }
+        for (int i = 0; i < t.n[l]; ++i) z[t.pts[l][i]] = t.dinv[l][i] * r[t.pts[l][i]];
+        std::vector<float> y, tb(t.box[l], 0.f), rc, zc;
+        apply(l, z, y);
+        for (int i = 0; i < t.n[l]; ++i) tb[t.pts[l][i]] = r[t.pts[l][i]] - y[t.pts[l][i]];
+        restrict_to(l, tb, rc);
+        cycle(l + 1, rc, zc);
+        for (int i = 0; i < t.n[l]; ++i) {
+            int u[3];
+            coords(l, t.pts[l][i], u);
+            z[t.pts[l][i]] += prolong_at(l, zc, u);
+        }
+        apply(l, z, y);
+        for (int i = 0; i < t.n[l]; ++i) z[t.pts[l][i]] += t.dinv[l][i] * (r[t.pts[l][i]] - y[t.pts[l][i]]);
+    }
+    void apply_pre(const Vec &r, Vec &z) const { vcycle(r, z); }
+    // z = M r on the fine level (compressed vectors in the fine point order)
+    void vcycle(const Vec &r, Vec &z) const
+    {
+        const MgLevel &A = *fine;
+        const size_t fbox = (size_t)A.B[0] * A.B[1] * A.B[2];
+        Vec ar;
+        spmv(A, r, ar);
+        std::vector<float> tb(fbox, 0.f), rc, zc;
+        for (int i = 0; i < A.n; ++i) tb[A.pts[i]] = (float)r[i] - c0 * (float)ar[i];
+        restrict_to(0, tb, rc);
+        cycle(1, rc, zc);
+        Vec z0(A.n), az;
+        for (int i = 0; i < A.n; ++i) {
+            int u[3];
+            coords(0, A.pts[i], u);
+            z0[i] = c0 * (float)r[i] + prolong_at(0, zc, u);
+        }
+        spmv(A, z0, az);
+        z.resize(A.n);
+        for (int i = 0; i < A.n; ++i) z[i] = (float)(z0[i] + c0 * (float)(r[i] - az[i]));
+    }
+};
+
+template <class Pre>
+static int pcg(const MgLevel &A, const Vec &b, const Pre *M, double tol, Vec &x)
 {
     const int n = A.n;
     x.assign(n, 0.0);
     Vec r = b, z, p, q;
-    if (M) M->vcycle(0, r, z);
+    if (M) M->apply_pre(r, z);
     else z = r;
     p = z;
     double rz = dot(r, z);
@@ -146,7 +291,7 @@ static int pcg(const MgLevel &A, const Vec &b, const Mg *M, double tol, Vec &x)
             r[i] -= a * q[i];
         }
         if (std::sqrt(dot(r, r)) <= tol * bn) return it;
-        if (M) M->vcycle(0, r, z);
+        if (M) M->apply_pre(r, z);
         else z = r;
         const double rz2 = dot(r, z);
         for (int i = 0; i < n; ++i) p[i] = z[i] + (rz2 / rz) * p[i];
@@ -199,8 +344,29 @@ int main(int argc, char **argv)
         b[i] = 4.0 * M_PI * g1 * g2;
     }
     Vec x0, x1;
-    const int k0 = pcg(A, b, nullptr, 1e-9, x0);
+    const int k0 = pcg<Mg>(A, b, nullptr, 1e-9, x0);
     const int k1 = pcg(A, b, &mg, 1e-9, x1);
+    // the device tables of the same hierarchy, applied in FP32 as the solver does
+    MgTables T;
+    if (make_mg_tables(L, st, 3, 200, 0.7, T)) return 5;
+    int k2 = -1, n_exp1 = 0;
+    double rel2 = 1.0;
+    if (T.nlev >= 2) {
+        std::vector<MgLevel> lv2;
+        make_mg_levels(L, st, 3, 200, lv2);
+        MgT mt{&T, &lv2[0], 0.f};
+        for (int k = lv2[0].row[0]; k < lv2[0].row[1]; ++k)
+            if (lv2[0].col[k] == 0) mt.c0 = (float)(0.7 / lv2[0].val[k]);
+        Vec x2;
+        k2 = pcg(A, b, &mt, 1e-9, x2);
+        double d2 = 0.0, n2 = 0.0;
+        for (int i = 0; i < A.n; ++i) {
+            d2 += (x2[i] - x0[i]) * (x2[i] - x0[i]);
+            n2 += x0[i] * x0[i];
+        }
+        rel2 = std::sqrt(d2 / n2);
+        n_exp1 = T.n_exp[1];
+    }
     double d = 0.0, nx = 0.0;
     for (int i = 0; i < A.n; ++i) {
         d += (x1[i] - x0[i]) * (x1[i] - x0[i]);
@@ -211,7 +377,8 @@ int main(int argc, char **argv)
     std::printf("{\"levels\": [");
     for (size_t l = 0; l < mg.lv.size(); ++l) std::printf("%s%d", l ? ", " : "", mg.lv[l].n);
     std::printf("], \"n_stcl\": %d, \"cg_iter\": %d, \"pcg_iter\": %d, \"rel_diff\": %.3e, \"asym\": %.3e, "
-                "\"level1_max_nnz\": %d}\n",
-                2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz);
+                "\"level1_max_nnz\": %d, \"tables_levels\": %d, \"tables_pcg_iter\": %d, "
+                "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d}\n",
+                2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1]);
     return 0;
 }

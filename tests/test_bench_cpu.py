@@ -41,9 +41,18 @@ def test_traffic_only_from_a_profile_of_the_current_source(tmp_path, monkeypatch
 def test_kernel_sha_covers_the_solver_sources(tmp_path, monkeypatch):
     src = tmp_path / "paper_2011_07209_gb300" / "csrc"
     src.mkdir(parents=True)
-    for f in ("kernels.cu", "exx_dev.h", "kernels.h"):
+    for f in ("kernels.cu", "exx_dev.h", "kernels.h", "pair_rule.cuh"):
         (src / f).write_text(f"// {f}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     a = bench.kernel_sha()
     (src / "exx_dev.h").write_text("// changed\n")
     assert bench.kernel_sha() != a
+
+
+def test_algorithmic_bytes_multigrid():
+    n_pairs, it, ref, n_pe, n_me = 2, 15, 3, 1000, 2500
+    per_pair = 2 * n_me * 8 + 2 * n_me * 16 + 8 * n_pe
+    levels = [1000, 140, 20]
+    # 13 FP32 accesses per fine point-iteration, 8 per coarse point
+    assert bench.algorithmic_bytes(n_pairs, it, ref, n_pe, n_me, 4, levels) == \
+        it * (13 * n_pe * 4 + 8 * 4 * 160) + ref * 20 * n_pe + n_pairs * per_pair

@@ -67,3 +67,29 @@ def test_errors():
         exx.geometry(c["lattice"], c["n"], exx.make_params(fd_order=0))
     assert e.value.code == exx.ERR_ARG
     assert exx.lib().exx_geometry_query(None, None, None) == exx.ERR_ARG
+
+
+def test_dbox_layout_abi():
+    """exx_dbox_layout (host only): the smallest extent 2 halfwidth + 1 (clamped
+    to n), boxes centred on each centre's nearest grid point, a caller extent
+    accepted between that and n and refused outside."""
+    from paper_2011_07209_gb300 import exx
+    lat = 29.6 * np.array([[1.0, 0, 0], [0.1, 1.0, 0], [0.05, -0.08, 1.0]])
+    n = (150, 150, 150)
+    p = exx.make_params()
+    rng = np.random.default_rng(4)
+    cen = (rng.random((40, 3)) * 1.4 - 0.2) @ lat      # some centres outside the cell
+    dbox, lo = exx.dbox_layout(lat, n, cen, p)
+    hw = exx.dbox_halfwidth(lat, n, p)
+    assert np.array_equal(dbox, np.minimum(2 * hw + 1, n))
+    frac = cen @ np.linalg.inv(lat.T).T
+    frac -= np.floor(frac)
+    gc = np.floor(frac * np.asarray(n) + 0.5).astype(np.int64)
+    assert np.array_equal(lo, gc - dbox // 2)
+    big, lo2 = exx.dbox_layout(lat, n, cen, p, dbox=dbox + 2)
+    assert np.array_equal(big, dbox + 2) and np.array_equal(lo2, gc - (dbox + 2) // 2)
+    import pytest
+    with pytest.raises(ValueError):
+        exx.dbox_layout(lat, n, cen, p, dbox=dbox - 1)
+    with pytest.raises(ValueError):
+        exx.dbox_layout(lat, n, cen, p, dbox=(151, 151, 151))

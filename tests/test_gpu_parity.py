@@ -220,3 +220,63 @@ def test_plan_matches_oracle_geometry(ctx):
         assert info["n_pe_pair"] == npe and info["n_me_pair"] == m.shape[0]
         assert np.array_equal(info["dirs"], st["dirs"])
         assert np.allclose(info["coef"], st["coef"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("cell", ["cubic", "triclinic", "monoclinic"])
+def test_multigrid_preconditioned_cg(ctx, cell):
+    """The mixed path with and without the multigrid preconditioner: the same
+    discrete solution (both against the oracle at the parity tolerances) from
+    far fewer iterations."""
+    from paper_2011_07209_gb300 import driver, exx
+    if cell == "cubic":
+        ws, rp = synth.make_config(1), (8.0, 6.0, 8.0)
+    elif cell == "triclinic":
+        ws, rp = _small_triclinic(), (7.0, 5.0, 6.5)
+    else:
+        lat = 13.0 * np.array([[1.0, 0, 0], [0, 1.0, 0], [0.12, 0, 1.0]])
+        ws, rp = synth.water_cell(lat, (45, 47, 46), 3, 9), (7.0, 5.0, 6.5)
+    outs = {}
+    for pc in (exx.PRECOND_NONE, exx.PRECOND_MG):
+        p = exx.make_params(r_pair=rp[0], r_pe=rp[1], r_me=rp[2], tol=1e-10, precision=exx.MIXED, precond=pc)
+        cr = driver.prepare(ctx, ws, p)
+        g = driver.run(ctx, cr)
+        g["dxx"] = cr.dxx.cpu().numpy()
+        outs[pc] = (g, cr)
+    g_mg, cr = outs[exx.PRECOND_MG]
+    g_cg, _ = outs[exx.PRECOND_NONE]
+    o = _oracle(ws, *rp, 1e-10, cr.dbox, cr.dbox_lo_np)
+    _compare(g_mg, o, "mixed")
+    _compare(g_cg, o, "mixed")
+    assert g_mg["status"] == 0
+    assert g_mg["total_cg_iter"] < 0.25 * g_cg["total_cg_iter"], (g_mg["total_cg_iter"], g_cg["total_cg_iter"])
+    assert g_mg["max_cg_iter"] <= 40
+
+
+def test_sharded_solves_sum_to_the_whole(ctx):
+    """exx_plan_set_shard on one GPU: the shards of 3 ranks, solved one after the
+    other, hold every pair once (per-pair outputs of other ranks' pairs are
+    zero), and their partial E_xx, Pi and D_xx add up to the unsharded solve."""
+    from paper_2011_07209_gb300 import driver, exx
+    ws = _small_triclinic()
+    p = exx.make_params(r_pair=7.0, r_pe=5.0, r_me=6.5, tol=1e-10, precision=exx.MIXED)
+    cr = driver.prepare(ctx, ws, p)
+    whole = driver.run(ctx, cr)
+    d_whole = cr.dxx.cpu().numpy()
+    owner = exx.pair_partition(ws.lattice, ws.n, p, whole["pairs"], 3)
+    e_sum, pi_sum, d_sum, seen = 0.0, 0.0, 0.0, np.zeros(whole["n_pairs"], int)
+    for rank in range(3):
+        crr = driver.prepare(ctx, ws, p)
+        crr.plan.set_shard(rank, 3)
+        part = driver.run(ctx, crr)
+        assert part["n_pairs"] == whole["n_pairs"]
+        mine = owner == rank
+        assert np.all(part["pair_e"][~mine] == 0.0)
+        assert np.allclose(part["pair_e"][mine], whole["pair_e"][mine], rtol=1e-7, atol=0)
+        seen += mine
+        e_sum += part["e_xx"]
+        pi_sum = pi_sum + part["stress"]
+        d_sum = d_sum + crr.dxx.cpu().numpy()
+    assert np.all(seen == 1)
+    assert e_sum == pytest.approx(whole["e_xx"], rel=1e-7)
+    assert np.abs(pi_sum - whole["stress"]).max() < 1e-10
+    assert np.abs(d_sum - d_whole).max() < 1e-8

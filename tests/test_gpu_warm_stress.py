@@ -159,3 +159,44 @@ def test_warm_start_falls_back_to_multipole_guess_for_large_steps(ctx):
         if k == 1:
             assert w["n_warm"] < 0.5 * w["n_pairs"]
             assert w["total_cg_iter"] < 1.1 * g["total_cg_iter"]
+
+
+def test_strain_triggered_reassembly(ctx):
+    """Frozen proto-subdomains along a trajectory whose strain grows step by step
+    (Sec. III B 2): once the Green-Lagrange strain against the plan's reference
+    cell exceeds the threshold, the subdomains are re-assembled from the current
+    cell (a new plan, no warm start carried over); the step after that matches
+    the oracle with the new reference cell, and the steps before it the oracle
+    with the old one."""
+    from paper_2011_07209_gb300 import driver, exx
+    ws0 = synth.make_config(1)
+    eps = np.array([[3e-3, 1e-3, 0.0], [1e-3, -2e-3, 1e-3], [0.0, 1e-3, 2e-3]])   # per step
+    steps, ws = [ws0], ws0
+    for _ in range(3):
+        ws = synth.strained(ws, eps)
+        steps.append(ws)
+    policy = exx.Reassembly(eps_max=6e-3)
+    kw = dict(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, precision=exx.MIXED, frozen=True, warm_start=True)
+    p = exx.make_params(**kw)
+    lat_ref, since = ws0.lattice.copy(), 0
+    plan = exx.Plan(ctx, lat_ref, ws0.n, p, ws0.n_orb, ws0.box)
+    reassembled_at = None
+    for k, ws in enumerate(steps):
+        if policy.due(lat_ref, ws.lattice, since):
+            plan.close()
+            lat_ref, since = ws.lattice.copy(), 0
+            plan = exx.Plan(ctx, lat_ref, ws.n, p, ws.n_orb, ws.box)
+            reassembled_at = k if reassembled_at is None else reassembled_at
+        cr = driver.prepare(ctx, ws, p, plan=plan)
+        g = driver.run(ctx, cr)
+        assert g["status"] == 0
+        if since == 0 and k > 0:
+            assert g["n_warm"] == 0          # a fresh plan starts without previous solutions
+        o = oracle.exx(ws, oracle.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-10, lattice0=lat_ref),
+                       dbox=cr.dbox, dbox_lo=cr.dbox_lo_np)
+        assert np.array_equal(g["pairs"], o["pairs"])
+        assert g["e_xx"] == pytest.approx(o["e_xx"], rel=1e-7)
+        assert np.abs(g["stress"] - o["stress"]).max() < 1e-8
+        assert np.abs(cr.dxx.cpu().numpy() - o["dxx"]).max() < 1e-6
+        since += 1
+    assert reassembled_at == 2                 # strain ~4e-3 after one step, ~8e-3 after two

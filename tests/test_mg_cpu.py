@@ -1,4 +1,4 @@
-"""Host multigrid hierarchy (make_mg_levels in csrc/plan.cpp) built from the
+"""Host multigrid hierarchy (make_mg_levels, make_mg_tables in csrc/plan.cpp) built from the
 planner's own offsets, layout and NK stencil: its Galerkin operators must be
 symmetric, and as a V(1,1) preconditioner of CG on the PE Poisson problem it
 must reach the plain-CG solution in far fewer iterations.  The harness
@@ -41,3 +41,9 @@ def test_vcycle_preconditioned_cg(harness, cell, n_stcl):
     assert r["cg_iter"] > 150                       # plain CG to 1e-9
     assert 0 < r["pcg_iter"] <= 20                  # V(1,1)-preconditioned CG to 1e-9
     assert r["rel_diff"] < 1e-8                     # the same discrete solution
+    # the device form of the hierarchy (interior / explicit rows, padded boxes,
+    # dense inverse on the coarsest level), applied in FP32 as the solver does
+    assert r["tables_levels"] == len(lv) + 1         # down to <= 200 points
+    assert 0 < r["tables_pcg_iter"] <= 20
+    assert r["tables_rel_diff"] < 1e-8
+    assert 0 < r["tables_level1_explicit"] < r["tables_level1_n"]

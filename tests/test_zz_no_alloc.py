@@ -53,6 +53,7 @@ def test_noalloc_pair_list_matches_solve(case):
         assert np.array_equal(rows[:cap2].cpu().numpy(), ref[:cap2])
         assert np.all(rows[cap2:].cpu().numpy() == -7)
         # no orbitals: zero pairs, nothing written
+        rows = torch.full((cap2 + 5, 8), -7, dtype=torch.int32, device="cuda")
         n.fill_(-1)
         assert exx.pair_list_noalloc(ws.lattice, ws.n, cen, 0, r_pair, rows, n) == exx.OK
         torch.cuda.synchronize()
