@@ -458,18 +458,22 @@ def run_trajectory(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     c = synth.CONFIGS[5]
+    shard = args.shard and world > 1
     log("generating the trajectory")
-    ws0 = traj_cell(rank)
-    steps = traj_steps(ws0, rank)
+    ws0 = traj_cell(0 if shard else rank)      # sharded: every rank holds the same cell
+    steps = traj_steps(ws0, 0 if shard else rank)
     log("trajectory ready; plan and device inputs")
     box = steps[0].box
     ctx = exx.Context(local_rank)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
-    mk = dict(r_pair=c["r_pair"], r_pe=c["r_pe"], r_me=c["r_me"], tol=c["tol"], frozen=True)
+    # a pair that fails to converge stops at 3000 iterations (plain CG needs about 250)
+    mk = dict(r_pair=c["r_pair"], r_pe=c["r_pe"], r_me=c["r_me"], tol=c["tol"], frozen=True, max_iter=3000)
     pc = PRECONDS[args.precond]
     p = exx.make_params(precision=exx.MIXED, warm_start=args.warm, precond=pc, **mk)
     plan = exx.Plan(ctx, ws0.lattice, ws0.n, p, ws0.n_orb, box)
+    if shard:
+        plan.set_shard(rank, world)
     dbox = np.max([exx.dbox_layout(w.lattice, w.n, w.centres, p)[0] for w in steps], axis=0)
     dxx = torch.zeros((ws0.n_orb,) + tuple(int(b) for b in dbox), dtype=torch.float64, device="cuda")
     runs = [driver.prepare(ctx, w, p, plan=plan, dxx=dxx, device=local_rank) for w in steps]
@@ -502,6 +506,8 @@ def run_trajectory(args, rank, world, local_rank):
     for k in range(args.steps):
         out = driver.run(ctx, runs[k % N_MD], pair_outputs=False, stream=sh)
         solve_ms.append(ctx.timing()["solve_ms"])
+        if shard:   # E_xx, sigma, Pi and D_xx summed over the ranks (NCCL all-reduce)
+            driver.reduce_shards(out, runs[k % N_MD].dxx, dist)
         n_pairs += out["n_pairs"]
         tot_iter += out["total_cg_iter"]
         tot_ref += out["total_refine"]
@@ -513,6 +519,8 @@ def run_trajectory(args, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     elapsed, all_pairs = reduce_over_ranks(ev0.elapsed_time(ev1), n_pairs, dist, "cuda")
+    if shard:
+        all_pairs = n_pairs          # one cell shared by the ranks: its pairs count once
     ms_step = elapsed / args.steps
     value = all_pairs / (elapsed / 1e3)
     avg_solve = sum(solve_ms) / len(solve_ms)
@@ -524,7 +532,7 @@ def run_trajectory(args, rank, world, local_rank):
     # end to end through the C ABI with pinned host buffers: every step copies its
     # orbitals in and its D_xx out inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not shard:
         log("end-to-end leg: pinned host buffers")
         n_e2e = min(args.steps, N_MD)
         n_buf = min(n_e2e, 4)
@@ -538,12 +546,13 @@ def run_trajectory(args, rank, world, local_rank):
             lo_h[...] = w.box_lo
             dlo_h = torch.empty(runs[0].dbox_lo_np.shape, dtype=torch.int32, pin_memory=True).numpy()
             dlo_h[...] = runs[si].dbox_lo_np
+            # the orbitals structure holds raw pointers: keep the buffers alive beside it
             host.append((w, exx.make_orbitals(w.n_orb, w.box, cen_h, lo_h, phi_h, exx.MEM_HOST), dlo_h,
-                         phi_h.nbytes + cen_h.nbytes + lo_h.nbytes + dlo_h.nbytes))
+                         phi_h.nbytes + cen_h.nbytes + lo_h.nbytes + dlo_h.nbytes, (phi_h, cen_h, lo_h)))
         del dxx, runs
         torch.cuda.empty_cache()
         dxx_h = torch.empty((ws0.n_orb,) + tuple(int(x) for x in dbox), dtype=torch.float64, pin_memory=True).numpy()
-        w, orb, dlo_h, _ = host[0]
+        w, orb, dlo_h, _, _ = host[0]
         log("end-to-end leg: warm call")
         exx.solve(ctx, plan, w.lattice, w.n, orb, exx.make_result(dxx_h, dbox, dlo_h, exx.MEM_HOST), stream=sh)
         torch.cuda.synchronize()
@@ -552,7 +561,7 @@ def run_trajectory(args, rank, world, local_rank):
         e0.record(stream)
         e2e_pairs, h2d = 0, 0
         for k in range(n_e2e):
-            w, orb, dlo_h, nb = host[k % n_buf]
+            w, orb, dlo_h, nb, _ = host[k % n_buf]
             res = exx.make_result(dxx_h, dbox, dlo_h, exx.MEM_HOST)
             exx.solve(ctx, plan, w.lattice, w.n, orb, res, stream=sh)
             e2e_pairs += res.n_pairs
@@ -571,7 +580,7 @@ def run_trajectory(args, rank, world, local_rank):
     # plain FP64 GPU path beside the mixed one on a pair sample of MD step 0 (the
     # pairs of its first --arm-orbitals MLWFs), and both against the FP64 oracle
     arms, accuracy, cpu = None, None, None
-    if rank == 0 and not args.no_arms:
+    if rank == 0 and not args.no_arms and not shard:
         sub = steps[0].subset(args.arm_orbitals) if args.arm_orbitals < ws0.n_orb else steps[0]
         arms, gouts, gruns = {}, {}, {}
         for name, prec in (("mixed", exx.MIXED), ("fp64", exx.FP64)):
@@ -618,7 +627,8 @@ def run_trajectory(args, rank, world, local_rank):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "strong" if shard else "weak",
             "vs_baseline": None, "dtype": "mixed-f32-f64", "data": "synthetic",
             "config": {"workload": TRAJ_WORKLOAD, "md_steps_cycled": N_MD, "schedule": plan.schedule(),
                        "pairs_per_step": n_pairs / args.steps,
@@ -627,7 +637,8 @@ def run_trajectory(args, rank, world, local_rank):
                        "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_true_residuals": tot_ref / max(n_pairs, 1),
                        "ctas": info["ctas"], "threads": info["threads"], "ctas_per_pair": info["cluster"],
                        "l2": "inputs larger than L2 (orbital boxes 2 GB per MD step, D_xx 16.8 GB)",
-                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+                       "parallelism": (f"pair-sharded{world}" if shard else f"replicas{world}") if world > 1
+                       else "single-gpu"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair_solve<float>",
                          "algorithmic_bytes_per_launch": bytes_launch / args.steps, "avg_launch_ms": avg_solve,
@@ -767,6 +778,9 @@ def main():
     ap.add_argument("--arm-orbitals", type=int, default=256,
                     help="the FP64 arm and the accuracy check solve the pairs of the first K MLWFs of MD step 0")
     ap.add_argument("--warm", action="store_true", help="trajectory256 with warm-started CG (previous MD step)")
+    ap.add_argument("--shard", action="store_true",
+                    help="trajectory256 under torchrun: the ranks share one cell's pairs (LPT partition, all-reduce "
+                         "of E, sigma and D per step; strong scaling) instead of solving one cell each")
     ap.add_argument("--autotune", type=int, default=0,
                     help="autotune each plan's solver schedule on this many pairs first (0: the default schedule)")
     ap.add_argument("--workload", default="trajectory256", choices=["trajectory256", "water64"] + sorted(WORKLOADS),

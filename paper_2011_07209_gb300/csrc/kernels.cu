@@ -2134,6 +2134,8 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 ((float *)qv)[k] = 0.f;
                 ((float *)ev)[k] = 0.f;
                 reinterpret_cast<float *>(slot + W.off_zf)[off] = 0.f;
+            } else {
+                ((double *)qv)[k] = 0.0;   // q of the FP64 CG (compressed); the other paths read this region as a box
             }
         }
         for (int h = tid; h < S.n_halo; h += nt) vbox[S.halo_off[h]] = 0.0;

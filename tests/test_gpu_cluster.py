@@ -79,7 +79,9 @@ def test_cluster_matches_cta_solver_full_size(ctxs):
     from paper_2011_07209_gb300 import exx
     cl, cta = ctxs
     ws = synth.make_config(2)
-    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, precision=exx.MIXED, guess=False)
+    # both plain CG (the cluster solver has no preconditioner), so that the iterates agree
+    p = exx.make_params(r_pair=8.0, r_pe=6.0, r_me=8.0, tol=1e-9, precision=exx.MIXED, guess=False,
+                        precond=exx.PRECOND_NONE)
     a = _run(cl, ws, p, want_d=True)
     b = _run(cta, ws, p, want_d=True)
     assert a["info"]["cluster"] == 16 and b["info"]["cluster"] == 1
