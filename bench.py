@@ -631,8 +631,7 @@ def run_trajectory(args, rank, world, local_rank):
             "scaling": "strong" if shard else "weak",
             "vs_baseline": None, "dtype": "mixed-f32-f64", "data": "synthetic",
             "config": {"workload": TRAJ_WORKLOAD, "md_steps_cycled": N_MD, "schedule": plan.schedule(),
-                       "pairs_per_step": n_pairs / args.steps,
-                   "schedules": schedules, "autotuned": bool(args.autotune), "n_pe": info["n_pe_pair"],
+                       "pairs_per_step": n_pairs / args.steps, "autotuned": bool(args.autotune), "n_pe": info["n_pe_pair"],
                        "n_me": info["n_me_pair"], "n_stcl": info["n_stcl"],
                        "mean_cg_iter": tot_iter / max(n_pairs, 1), "mean_true_residuals": tot_ref / max(n_pairs, 1),
                        "ctas": info["ctas"], "threads": info["threads"], "ctas_per_pair": info["cluster"],

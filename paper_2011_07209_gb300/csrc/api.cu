@@ -251,13 +251,15 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         MgLevelDev &v = G.lv[l];
         v.n = T.n[l];
         v.K = T.K[l];
+        v.n_int = T.n_int[l];
+        v.n_exp = T.n_exp[l];
         for (int a = 0; a < 3; ++a) v.Bp[a] = T.Bp[l][a];
         v.box = T.box[l];
         v.stride = (T.box[l] + 63) & ~63LL;
         v.off = off;
         off += 3 * v.stride;
-        if ((e = mg_put(p, s, T.pts[l], &v.pts)) || (e = mg_put(p, s, T.wrow[l], &v.wrow)) ||
-            (e = mg_put(p, s, T.wexp[l], &v.wexp)) || (e = mg_put(p, s, T.dinv[l], &v.dinv)))
+        if ((e = mg_put(p, s, T.pts[l], &v.pts)) || (e = mg_put(p, s, T.wexp[l], &v.wexp)) ||
+            (e = mg_put(p, s, T.dinv[l], &v.dinv)) || (e = mg_put(p, s, T.dbox[l], &v.dbox)))
             return e;
         for (int k = 0; k < T.K[l]; ++k) {
             G.kd[l][k] = T.kd[l][k];

@@ -20,14 +20,15 @@ constexpr int kMgPadDev = 2;
 constexpr int kMgCoarsestDev = 256;
 struct MgLevelDev {
     int n, K;                      // active points, pattern size
+    int n_int, n_exp;              // interior rows (the first n_int points), rows with their own weights
     int Bp[3];                     // padded box
     long long box;                 // padded box elements
     long long off;                 // float offset of the level's R, Z, T boxes in the slot's region
     long long stride;              // floats between R, Z and T
     const int32_t *pts;            // [n] padded box offset of each active point
-    const int32_t *wrow;           // [n] -1 interior row, else its row in wexp
-    const float *wexp;             // [n_exp][K]
+    const float *wexp;             // [K][n_exp] weights of the non-interior rows, pattern-major
     const float *dinv;             // [n] omega / diag(A_l)
+    const float *dbox;             // [box] the same on the padded box, zero at inactive points
 };
 struct MgDev {
     int nlev;                      // levels including the fine one; 0: no hierarchy

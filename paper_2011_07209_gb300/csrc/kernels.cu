@@ -1089,9 +1089,10 @@ struct MgSm {                      // the hierarchy of the pair's set, in shared
     float c0;                      // omega / diag(A) of the fine level
     float dscale;                  // omega / (the tables' omega): scales the coarse dinv
     int n[kMgLevelsDev], K[kMgLevelsDev], Bp1[kMgLevelsDev], Bp2[kMgLevelsDev];
+    int n_int[kMgLevelsDev], n_exp[kMgLevelsDev];
     float *R[kMgLevelsDev], *Z[kMgLevelsDev], *T[kMgLevelsDev];
-    const int32_t *pts[kMgLevelsDev], *wrow[kMgLevelsDev];
-    const float *wexp[kMgLevelsDev], *dinv[kMgLevelsDev];
+    const int32_t *pts[kMgLevelsDev];
+    const float *wexp[kMgLevelsDev], *dinv[kMgLevelsDev], *dbox[kMgLevelsDev];
     const float *cinv;
     int koff[kMgLevelsDev][kMgKDev];
     float wint[kMgLevelsDev][kMgKDev];
@@ -1190,41 +1191,78 @@ __device__ __forceinline__ float mg_prolong_at(const MgSm &m, int l, int u0, int
     return w0 * w1 * s;
 }
 
-// y = A_l x at active point i of coarse level l (x: a padded box of level l).
-__device__ __forceinline__ float mg_apply_row(const MgSm &m, int l, int i, const float *__restrict__ x)
+struct MgScalars {
+    double rz, rmax, S;
+    float alpha, beta;
+    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+};
+__shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid path
+__shared__ MgScalars g_mg_cs;
+
+// (A_l x) at active point i (box offset o) of coarse level l; with DX, x is the
+// product dbox * x (the Jacobi-smoothed vector, formed on the fly).  Four
+// independent partial sums keep several loads in flight.
+template <bool DX>
+__device__ __forceinline__ float mg_row(int l, int i, int o, const float *__restrict__ x)
 {
-    const int o = m.pts[l][i];
+    const MgSm &m = g_mg_sm;
     const int K = m.K[l];
-    const int wr = m.wrow[l][i];
-    float s = 0.f;
-    if (wr < 0) {
-        for (int k = 0; k < K; ++k) s += m.wint[l][k] * x[o + m.koff[l][k]];
+    const int *koff = m.koff[l];
+    const float *__restrict__ db = m.dbox[l];
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    auto xv = [&](int k) {
+        const int q = o + koff[k];
+        return DX ? __ldg(db + q) * x[q] : x[q];
+    };
+    const int e = i - m.n_int[l];
+    int k = 0;
+    if (e < 0) {
+        const float *w = m.wint[l];
+        for (; k + 4 <= K; k += 4) {
+            s0 += w[k] * xv(k);
+            s1 += w[k + 1] * xv(k + 1);
+            s2 += w[k + 2] * xv(k + 2);
+            s3 += w[k + 3] * xv(k + 3);
+        }
+        for (; k < K; ++k) s0 += w[k] * xv(k);
     } else {
-        const float *w = m.wexp[l] + (size_t)wr * K;
-        for (int k = 0; k < K; ++k) s += __ldg(w + k) * x[o + m.koff[l][k]];
+        const int ne = m.n_exp[l];
+        const float *__restrict__ w = m.wexp[l] + e;
+        for (; k + 4 <= K; k += 4) {
+            s0 += __ldg(w + (size_t)k * ne) * xv(k);
+            s1 += __ldg(w + (size_t)(k + 1) * ne) * xv(k + 1);
+            s2 += __ldg(w + (size_t)(k + 2) * ne) * xv(k + 2);
+            s3 += __ldg(w + (size_t)(k + 3) * ne) * xv(k + 3);
+        }
+        for (; k < K; ++k) s0 += __ldg(w + (size_t)k * ne) * xv(k);
     }
-    return s;
+    return (s0 + s1) + (s2 + s3);
 }
 
 // Z_1 = M_1 R_1: the V(1,1) cycle on the coarse levels 1 .. nlev-1.
-__device__ __noinline__ void mg_coarse_cycle(const MgSm &m)
+__device__ __noinline__ void mg_coarse_cycle()
 {
+    const MgSm &m = g_mg_sm;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int L = m.nlev - 1;   // coarsest
-    // down: pre-smoothing from zero, residual, restriction
+    // down: residual of the Jacobi-smoothed guess Z = D R (formed on the fly), restriction
     for (int l = 1; l < L; ++l) {
         const int *pts = m.pts[l];
-        for (int i = tid; i < m.n[l]; i += nt) m.Z[l][pts[i]] = m.dscale * __ldg(m.dinv[l] + i) * m.R[l][pts[i]];
+        const float *R = m.R[l];
+        float *T = m.T[l];
+        const float ds = m.dscale;
+        for (int i = tid; i < m.n[l]; i += nt) {
+            const int o = pts[i];
+            T[o] = R[o] - ds * mg_row<true>(l, i, o, R);
+        }
         __syncthreads();
-        for (int i = tid; i < m.n[l]; i += nt) m.T[l][pts[i]] = m.R[l][pts[i]] - mg_apply_row(m, l, i, m.Z[l]);
-        __syncthreads();
-        mg_restrict(m, l, m.T[l], m.Bp1[l], m.Bp2[l], kMgPadDev);
+        mg_restrict(m, l, T, m.Bp1[l], m.Bp2[l], kMgPadDev);
         __syncthreads();
     }
     // coarsest: z = A_L^-1 r, one warp per row
     {
         const int n = m.n[L];
-        float *cr = const_cast<float *>(m.cr);
+        float *cr = g_mg_sm.cr;
         for (int i = tid; i < n; i += nt) cr[i] = m.R[L][m.pts[L][i]];
         __syncthreads();
         const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
@@ -1238,18 +1276,29 @@ __device__ __noinline__ void mg_coarse_cycle(const MgSm &m)
         }
         __syncthreads();
     }
-    // up: coarse correction, post-smoothing
+    // up: Z = D R + P Z_{l+1}, then post-smoothing Z += D (R - A Z)
     for (int l = L - 1; l >= 1; --l) {
         const int *pts = m.pts[l];
+        const float *R = m.R[l];
+        float *Z = m.Z[l], *T = m.T[l];
+        const float ds = m.dscale;
         for (int i = tid; i < m.n[l]; i += nt) {
+            const int o = pts[i];
             int u0, u1, u2;
-            mg_coords(pts[i], m.Bp1[l], m.Bp2[l], u0, u1, u2);
-            m.Z[l][pts[i]] += mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
+            mg_coords(o, m.Bp1[l], m.Bp2[l], u0, u1, u2);
+            Z[o] = ds * __ldg(m.dinv[l] + i) * R[o] +
+                   mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
         }
         __syncthreads();
-        for (int i = tid; i < m.n[l]; i += nt) m.T[l][pts[i]] = m.R[l][pts[i]] - mg_apply_row(m, l, i, m.Z[l]);
+        for (int i = tid; i < m.n[l]; i += nt) {
+            const int o = pts[i];
+            T[o] = R[o] - mg_row<false>(l, i, o, Z);
+        }
         __syncthreads();
-        for (int i = tid; i < m.n[l]; i += nt) m.Z[l][pts[i]] += m.dscale * __ldg(m.dinv[l] + i) * m.T[l][pts[i]];
+        for (int i = tid; i < m.n[l]; i += nt) {
+            const int o = pts[i];
+            Z[o] += ds * __ldg(m.dinv[l] + i) * T[o];
+        }
         __syncthreads();
     }
 }
@@ -1282,20 +1331,33 @@ __device__ __forceinline__ double mg_precondition(const CgMixed &cg, const MgSm 
     __syncthreads();
     mg_restrict(m, 0, zout, B1, B2, 0);
     __syncthreads();
-    mg_coarse_cycle(m);
-    // z0 = c0 r + P Z_1 on PE
-    for (int g = tid; g < ng; g += nt) {
-        const int32_t gw = __ldg(grp + g);
-        const int off = (gw >> 4) << 2, mask = gw & 15;
-        int u0, u1, u2;
-        mg_coords(off, B1, B2, u0, u1, u2);
-        const float4 r = ld4(rf + off);
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        const float rv[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (mask & (1 << i)) z[i] = c0 * rv[i] + mg_prolong_at(m, 0, u0, u1, u2 + i);
-        st4(zf + off, z[0], z[1], z[2], z[3]);
+    mg_coarse_cycle();
+    // z0 = c0 r + P Z_1 on PE.  The group's four points u2 .. u2+3 (u2 even, a
+    // multiple of 4) take their last-axis parents from the three level-1 values
+    // at u2/2, u2/2 + 1, u2/2 + 2 of each (x, y) parent row.
+    {
+        const float *Z1 = m.Z[1];
+        const int cB1 = m.Bp1[1], cB2 = m.Bp2[1];
+        for (int g = tid; g < ng; g += nt) {
+            const int32_t gw = __ldg(grp + g);
+            const int off = (gw >> 4) << 2, mask = gw & 15;
+            int u0, u1, u2;
+            mg_coords(off, B1, B2, u0, u1, u2);
+            const int a0 = u0 >> 1, a1 = u1 >> 1, n0 = (u0 & 1) + 1, n1 = (u1 & 1) + 1;
+            float c_0 = 0.f, c_1 = 0.f, c_2 = 0.f;
+            for (int x = 0; x < n0; ++x)
+                for (int y = 0; y < n1; ++y) {
+                    const float *row =
+                        Z1 + ((size_t)(a0 + x + kMgPadDev) * cB1 + (a1 + y + kMgPadDev)) * cB2 + (u2 >> 1) + kMgPadDev;
+                    c_0 += row[0];
+                    c_1 += row[1];
+                    c_2 += row[2];
+                }
+            const float wxy = (n0 == 2 ? 0.5f : 1.f) * (n1 == 2 ? 0.5f : 1.f);
+            const float4 r = ld4(rf + off);
+            st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f, (mask & 2) ? c0 * r.y + wxy * 0.5f * (c_0 + c_1) : 0.f,
+                (mask & 4) ? c0 * r.z + wxy * c_1 : 0.f, (mask & 8) ? c0 * r.w + wxy * 0.5f * (c_1 + c_2) : 0.f);
+        }
     }
     __syncthreads();
     // z = z0 + c0 (r - A z0) = z0 + c0 (r + L z0), and <r, z>
@@ -1316,14 +1378,6 @@ __device__ __forceinline__ double mg_precondition(const CgMixed &cg, const MgSm 
     block_sum_df<1>(a, reinterpret_cast<float2 *>(cg.red));
     return (double)a[0].hi + (double)a[0].lo;
 }
-
-struct MgScalars {
-    double rz, rmax, S;
-    float alpha, beta;
-    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
-};
-__shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid path
-__shared__ MgScalars g_mg_cs;
 
 // The mixed-precision solve of one pair with the multigrid preconditioner (see
 // the comment above MgSm).  zf: one more dense FP32 box; mgbase: the slot's
@@ -1370,9 +1424,11 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                 m.Z[l] = mgbase + v.off + v.stride;
                 m.T[l] = mgbase + v.off + 2 * v.stride;
                 m.pts[l] = v.pts;
-                m.wrow[l] = v.wrow;
+                m.n_int[l] = v.n_int;
+                m.n_exp[l] = v.n_exp;
                 m.wexp[l] = v.wexp;
                 m.dinv[l] = v.dinv;
+                m.dbox[l] = v.dbox;
             }
         }
         for (int l = 1; l < G.nlev; ++l)

@@ -635,8 +635,13 @@ static int mg_coarsen(const MgLevel &f, MgLevel &c)
                     const long long o = ((long long)cc[0][x] * c.B[1] + cc[1][y]) * c.B[2] + cc[2][z];
                     pbox[(size_t)i * 8 + k] = o;
                     pw[(size_t)i * 8 + k] = ww[0][x] * ww[1][y] * ww[2][z];
-                    c.idx[(size_t)o] = 0;
                 }
+        // the coarse points are the fine points at even coordinates: each has its
+        // own weight-1 child, so the columns of P are independent and P^T A P
+        // stays positive definite (parents of odd boundary points that are not
+        // coarse points drop out of P)
+        if (!(u[0] & 1) && !(u[1] & 1) && !(u[2] & 1))
+            c.idx[(size_t)(((long long)(u[0] >> 1) * c.B[1] + (u[1] >> 1)) * c.B[2] + (u[2] >> 1))] = 0;
     }
     c.pts.clear();
     for (long long o = 0; o < cbox; ++o)
@@ -847,28 +852,45 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             ++K;
         }
         r.K[l] = K;
-        r.wrow[l].assign(A.n, -1);
-        r.dinv[l].resize(A.n);
-        std::vector<double> w(K);
+        // rows of A_l over the pattern; interior rows first, then the others
+        std::vector<double> w((size_t)A.n * K, 0.0), diag(A.n, 0.0);
+        std::vector<char> interior(A.n, 0);
         for (int i = 0; i < A.n; ++i) {
-            std::fill(w.begin(), w.end(), 0.0);
+            double *wi = &w[(size_t)i * K];
             bool same = (A.row[i + 1] - A.row[i]) == K;
-            double diag = 0.0;
             for (int k = A.row[i]; k < A.row[i + 1]; ++k) {
                 int d[3];
                 const int kk = key(i, A.col[k], d);
                 if (kk < 0 || pidx[kk] < 0) return EXX_OK;   // an entry outside the interior pattern
-                w[pidx[kk]] = A.val[k];
-                if (A.col[k] == i) diag = A.val[k];
+                wi[pidx[kk]] = A.val[k];
+                if (A.col[k] == i) diag[i] = A.val[k];
             }
-            if (!(diag > 0.0)) return EXX_OK;
-            r.dinv[l][i] = (float)(omega / diag);
-            for (int k = 0; k < K && same; ++k)
-                same = std::fabs(w[k] - wint[k]) <= 1e-12 * std::fabs(wint[k]);
-            if (same) continue;
-            r.wrow[l][i] = r.n_exp[l]++;
-            for (int k = 0; k < K; ++k) r.wexp[l].push_back((float)w[k]);
+            if (!(diag[i] > 0.0)) return EXX_OK;
+            for (int k = 0; k < K && same; ++k) same = std::fabs(wi[k] - wint[k]) <= 1e-12 * std::fabs(wint[k]);
+            interior[i] = same;
         }
+        std::vector<int> order;
+        for (int pass = 1; pass >= 0; --pass)
+            for (int i = 0; i < A.n; ++i)
+                if (interior[i] == pass) order.push_back(i);   // i ascending: box-offset order within a part
+        int n_int = 0;
+        for (int i = 0; i < A.n; ++i) n_int += interior[i];
+        const int n_exp = A.n - n_int;
+        r.n_int[l] = n_int;
+        r.n_exp[l] = n_exp;
+        std::vector<int32_t> pts(A.n);
+        r.dinv[l].resize(A.n);
+        r.wexp[l].assign((size_t)K * n_exp, 0.f);
+        r.dbox[l].assign((size_t)r.box[l], 0.f);
+        for (int q = 0; q < A.n; ++q) {
+            const int i = order[q];
+            pts[q] = r.pts[l][i];
+            r.dinv[l][q] = (float)(omega / diag[i]);
+            r.dbox[l][(size_t)pts[q]] = r.dinv[l][q];
+            if (q >= n_int)
+                for (int k = 0; k < K; ++k) r.wexp[l][(size_t)k * n_exp + (q - n_int)] = (float)w[(size_t)i * K + k];
+        }
+        r.pts[l] = std::move(pts);
     }
     t = std::move(r);
     return EXX_OK;

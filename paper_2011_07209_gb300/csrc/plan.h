@@ -82,12 +82,14 @@ int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
 // CG (not in the paper, which uses plain CG: the preconditioner changes the
 // iterates, not the discrete equations or the stopping rule).  Level 0: the PE
 // points of the dense CG box with A = -L, the NK stencil with the halo moved to
-// the right-hand side (Dirichlet zero).  Level l + 1: the points of a box half
-// as fine that are parents of active level-l points, where a point at box
-// coordinate u has the parents floor(u/2) and ceil(u/2) along each axis
-// (trilinear prolongation, weight 1 on an even coordinate and 1/2 on each side of
-// an odd one), restriction its transpose, and the Galerkin operator
-// A_{l+1} = P^T A_l P.  Operators are CSR with columns sorted.
+// the right-hand side (Dirichlet zero).  Level l + 1: the active level-l points
+// at even box coordinates u, as the points c = u/2 of a box half as fine (each
+// coarse point has its own weight-1 child, so the columns of P are independent
+// and every Galerkin operator stays positive definite); a level-l point at u
+// interpolates from those of floor(u/2) and ceil(u/2) along each axis that are
+// coarse points (trilinear prolongation, weight 1 on an even coordinate and 1/2
+// on each side of an odd one), restriction is its transpose, and the Galerkin
+// operator A_{l+1} = P^T A_l P.  Operators are CSR with columns sorted.
 struct MgLevel {
     int B[3] = {};                 // box of the level (level 0: the dense CG box)
     int n = 0;                     // active points
@@ -107,7 +109,11 @@ int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
 // offsets: rows equal to the level's interior stencil (the row of the most
 // central point) take the shared weights wint, the others (rows that the
 // Dirichlet boundary of the subdomain truncates) their own K weights in wexp,
-// zero where the row has no entry.  dinv = omega / diag(A_l).  The coarsest
+// zero where the row has no entry.  The active points are ordered interior
+// rows first (n_int of them), then the others, each part by box offset, and
+// wexp is stored pattern-major ([K][n - n_int]), so that the lanes of a warp
+// take the same branch and read consecutive weights.  dinv = omega / diag(A_l),
+// per point and as a padded box (dbox, zero at inactive points).  The coarsest
 // level nlev-1 is solved exactly with the inverse of its operator (cinv,
 // row-major over its active points).  Every operator is FP32.
 constexpr int kMgPad = 2;          // margin of the coarse boxes (the coarse stencil reach)
@@ -123,10 +129,11 @@ struct MgTables {
     int kd[kMgMaxLevels][kMgMaxK] = {};             // pattern offsets (dx+2) | (dy+2) << 3 | (dz+2) << 6
     float wint[kMgMaxLevels][kMgMaxK] = {};
     int n_exp[kMgMaxLevels] = {};
+    int n_int[kMgMaxLevels] = {};                   // interior rows (the first n_int active points)
     std::vector<int32_t> pts[kMgMaxLevels];         // padded box offset of each active point
-    std::vector<int32_t> wrow[kMgMaxLevels];        // -1: interior row, else its row in wexp
-    std::vector<float> wexp[kMgMaxLevels];          // [n_exp][K]
+    std::vector<float> wexp[kMgMaxLevels];          // [K][n_exp], n_exp = n - n_int
     std::vector<float> dinv[kMgMaxLevels];
+    std::vector<float> dbox[kMgMaxLevels];          // dinv on the padded box
     std::vector<float> cinv;                        // [n][n] of the coarsest level
     long long slot_floats = 0;                      // three boxes per coarse level
 };

@@ -59,6 +59,7 @@ static void transfer(const MgLevel &f, const MgLevel &c, const Vec &in, Vec &out
             for (int y = 0; y < np[1]; ++y)
                 for (int z = 0; z < np[2]; ++z) {
                     const int j = c.idx[((size_t)cc[0][x] * c.B[1] + cc[1][y]) * c.B[2] + cc[2][z]];
+                    if (j < 0) continue;   // a parent that is not a coarse point
                     const double w = ww[0][x] * ww[1][y] * ww[2][z];
                     if (prolong) out[i] += w * in[j];
                     else out[j] += w * in[i];
@@ -151,12 +152,13 @@ struct MgT {
         y.assign(t.box[l], 0.f);
         for (int i = 0; i < t.n[l]; ++i) {
             const int o = t.pts[l][i];
-            const float *w = t.wrow[l][i] < 0 ? t.wint[l] : &t.wexp[l][(size_t)t.wrow[l][i] * t.K[l]];
+            const int e = i - t.n_int[l];   // explicit rows follow the interior ones
             float s = 0.f;
             for (int k = 0; k < t.K[l]; ++k) {
                 int d[3];
                 unpack(t.kd[l][k], d);
-                s += w[k] * x[o + (d[0] * t.Bp[l][1] + d[1]) * t.Bp[l][2] + d[2]];
+                const float w = e < 0 ? t.wint[l][k] : t.wexp[l][(size_t)k * t.n_exp[l] + e];
+                s += w * x[o + (d[0] * t.Bp[l][1] + d[1]) * t.Bp[l][2] + d[2]];
             }
             y[o] = s;
         }
