@@ -288,7 +288,7 @@ int exx_plan_set_schedule(exx_plan *plan, const exx_schedule *sched);
  * one fixed plain schedule).  Runs the plan's pair solver on the first
  * `sample_pairs` pairs of this cell (the whole path up to Step IV, no D_xx)
  * once for every candidate schedule -- the multigrid preconditioner with
- * omega in {0.6, 0.7, 0.8}, and plain CG, each with inner_shift in {10, 14} --
+ * omega in {0.7, 0.6, 0.8}, and plain CG, each with inner_shift in {14, 18} --
  * timing the solver launch with CUDA events on `stream`, twice per candidate
  * (the faster run counts), and keeps the fastest for the plan's later solves
  * (ties keep the earlier candidate, the order above).  `chosen` (may be NULL)

@@ -1199,44 +1199,55 @@ struct MgScalars {
 __shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid path
 __shared__ MgScalars g_mg_cs;
 
-// (A_l x) at active point i (box offset o) of coarse level l; with DX, x is the
-// product dbox * x (the Jacobi-smoothed vector, formed on the fly).  Four
-// independent partial sums keep several loads in flight.
-template <bool DX>
-__device__ __forceinline__ float mg_row(int l, int i, int o, const float *__restrict__ x)
+// Part of (A_l x) at active point i (box offset o) of coarse level l: the
+// pattern entries k = sub, sub + tpr, ... (tpr threads share a row on the small
+// levels).  Two independent partial sums keep several loads in flight.
+__device__ __forceinline__ float mg_row(int l, int i, int o, const float *__restrict__ x, int sub, int tpr)
 {
     const MgSm &m = g_mg_sm;
     const int K = m.K[l];
     const int *koff = m.koff[l];
-    const float *__restrict__ db = m.dbox[l];
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    auto xv = [&](int k) {
-        const int q = o + koff[k];
-        return DX ? __ldg(db + q) * x[q] : x[q];
-    };
+    float s0 = 0.f, s1 = 0.f;
     const int e = i - m.n_int[l];
-    int k = 0;
+    int k = sub;
     if (e < 0) {
         const float *w = m.wint[l];
-        for (; k + 4 <= K; k += 4) {
-            s0 += w[k] * xv(k);
-            s1 += w[k + 1] * xv(k + 1);
-            s2 += w[k + 2] * xv(k + 2);
-            s3 += w[k + 3] * xv(k + 3);
+        for (; k + tpr < K; k += 2 * tpr) {
+            s0 += w[k] * x[o + koff[k]];
+            s1 += w[k + tpr] * x[o + koff[k + tpr]];
         }
-        for (; k < K; ++k) s0 += w[k] * xv(k);
+        if (k < K) s0 += w[k] * x[o + koff[k]];
     } else {
         const int ne = m.n_exp[l];
         const float *__restrict__ w = m.wexp[l] + e;
-        for (; k + 4 <= K; k += 4) {
-            s0 += __ldg(w + (size_t)k * ne) * xv(k);
-            s1 += __ldg(w + (size_t)(k + 1) * ne) * xv(k + 1);
-            s2 += __ldg(w + (size_t)(k + 2) * ne) * xv(k + 2);
-            s3 += __ldg(w + (size_t)(k + 3) * ne) * xv(k + 3);
+        for (; k + tpr < K; k += 2 * tpr) {
+            s0 += __ldg(w + (size_t)k * ne) * x[o + koff[k]];
+            s1 += __ldg(w + (size_t)(k + tpr) * ne) * x[o + koff[k + tpr]];
         }
-        for (; k < K; ++k) s0 += __ldg(w + (size_t)k * ne) * xv(k);
+        if (k < K) s0 += __ldg(w + (size_t)k * ne) * x[o + koff[k]];
     }
-    return (s0 + s1) + (s2 + s3);
+    return s0 + s1;
+}
+
+// T = R - A_l X on the active points of coarse level l.  Levels with fewer
+// rows than half the CTA's threads give each row 2, 4 or 8 adjacent lanes,
+// which split the pattern and add their parts by shuffles.
+__device__ __forceinline__ void mg_resid(int l, const float *__restrict__ R, const float *__restrict__ X,
+                                         float *__restrict__ T)
+{
+    const MgSm &m = g_mg_sm;
+    const int n = m.n[l], nt = blockDim.x;
+    int tpr = 1;
+    while (tpr < 8 && n * tpr * 2 <= nt) tpr <<= 1;
+    const int lane = threadIdx.x & 31, sub = lane & (tpr - 1);
+    const unsigned gmask = ((1u << tpr) - 1u) << (lane & ~(tpr - 1));
+    const int *pts = m.pts[l];
+    for (int i = threadIdx.x / tpr; i < n; i += nt / tpr) {
+        const int o = pts[i];
+        float s = mg_row(l, i, o, X, sub, tpr);
+        for (int d = tpr >> 1; d > 0; d >>= 1) s += __shfl_xor_sync(gmask, s, d);
+        if (sub == 0) T[o] = R[o] - s;
+    }
 }
 
 // Z_1 = M_1 R_1: the V(1,1) cycle on the coarse levels 1 .. nlev-1.
@@ -1245,16 +1256,18 @@ __device__ __noinline__ void mg_coarse_cycle()
     const MgSm &m = g_mg_sm;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int L = m.nlev - 1;   // coarsest
-    // down: residual of the Jacobi-smoothed guess Z = D R (formed on the fly), restriction
+    // down: Jacobi smoothing from zero, Z = D R, its residual T = R - A Z, restriction
     for (int l = 1; l < L; ++l) {
         const int *pts = m.pts[l];
         const float *R = m.R[l];
-        float *T = m.T[l];
+        float *Z = m.Z[l], *T = m.T[l];
         const float ds = m.dscale;
         for (int i = tid; i < m.n[l]; i += nt) {
             const int o = pts[i];
-            T[o] = R[o] - ds * mg_row<true>(l, i, o, R);
+            Z[o] = ds * __ldg(m.dinv[l] + i) * R[o];
         }
+        __syncthreads();
+        mg_resid(l, R, Z, T);
         __syncthreads();
         mg_restrict(m, l, T, m.Bp1[l], m.Bp2[l], kMgPadDev);
         __syncthreads();
@@ -1290,10 +1303,7 @@ __device__ __noinline__ void mg_coarse_cycle()
                    mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
         }
         __syncthreads();
-        for (int i = tid; i < m.n[l]; i += nt) {
-            const int o = pts[i];
-            T[o] = R[o] - mg_row<false>(l, i, o, Z);
-        }
+        mg_resid(l, R, Z, T);
         __syncthreads();
         for (int i = tid; i < m.n[l]; i += nt) {
             const int o = pts[i];

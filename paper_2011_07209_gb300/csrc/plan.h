@@ -141,7 +141,7 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
 
 // Candidate schedules of the autotuner (exx_plan_autotune), in the order that
 // breaks ties: with a multigrid hierarchy, MG with omega 0.7, 0.6, 0.8, each
-// with inner_shift 14 then 10; then plain CG with inner_shift 14, 10.
+// with inner_shift 14 then 18; then plain CG with inner_shift 14, 18.
 std::vector<exx_schedule> schedule_candidates(bool mg, double omega_default);
 // Longest-processing-time partition of n jobs over n_ranks: jobs in order of
 // decreasing cost (equal costs keep their order), each given to the rank with
