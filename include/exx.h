@@ -152,7 +152,7 @@ typedef struct {
     int box[3];             /* orbital box extent */
     const double *centres;  /* [n_orb][3] Cartesian centres C_i, bohr */
     const int *box_lo;      /* [n_orb][3] first grid index of each box */
-    const double *phi;      /* [n_orb][box0][box1][box2] orbital values */
+    const double *phi;      /* [n_orb][box0][box1][box2] orbital values, FP64 (the only type) */
     int mem;                /* EXX_MEM_DEVICE or EXX_MEM_HOST for the three arrays */
 } exx_orbitals;
 
@@ -209,7 +209,7 @@ typedef struct {
  * exx_params at plan creation; chosen per plan by exx_plan_autotune. */
 typedef struct {
     int precond;            /* EXX_PRECOND_NONE or EXX_PRECOND_MG */
-    float omega;            /* weighted-Jacobi factor of the V-cycle, in (0, 1] (default 0.7) */
+    float omega;            /* weighted-Jacobi factor of the V-cycle, in (0, 1] (default 0.8) */
     int inner_shift;        /* reliable update (double-float true residual) once the FP32    */
                             /* residual fell by 2^-inner_shift, 4..22 (default 14)          */
     double ms;              /* exx_plan_autotune: measured solver time of the sample, ms    */
@@ -288,7 +288,7 @@ int exx_plan_set_schedule(exx_plan *plan, const exx_schedule *sched);
  * one fixed plain schedule).  Runs the plan's pair solver on the first
  * `sample_pairs` pairs of this cell (the whole path up to Step IV, no D_xx)
  * once for every candidate schedule -- the multigrid preconditioner with
- * omega in {0.7, 0.6, 0.8}, and plain CG, each with inner_shift in {14, 18} --
+ * omega in {0.8, 0.7, 0.6}, and plain CG, each with inner_shift in {14, 18} --
  * timing the solver launch with CUDA events on `stream`, twice per candidate
  * (the faster run counts), and keeps the fastest for the plan's later solves
  * (ties keep the earlier candidate, the order above).  `chosen` (may be NULL)

@@ -190,7 +190,7 @@ static bool simple_cubic(const exx_cell &c)
     return true;
 }
 
-constexpr double kMgOmega = 0.7;   // weighted-Jacobi smoothing of the multigrid V-cycle
+constexpr double kMgOmega = 0.8;   // weighted-Jacobi smoothing of the multigrid V-cycle
 constexpr int kMaxBatchCells = 64;  // cells of one exx_pairs_solve_batch call
 
 static void free_mg(exx_plan *p, int s)

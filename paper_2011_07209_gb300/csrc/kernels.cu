@@ -1256,20 +1256,27 @@ __device__ __noinline__ void mg_coarse_cycle()
     const MgSm &m = g_mg_sm;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int L = m.nlev - 1;   // coarsest
-    // down: Jacobi smoothing from zero, Z = D R, its residual T = R - A Z, restriction
+    // down: Jacobi smoothing from zero, Z = D R, its residual T = R - A Z, restriction.
+    // Level 1 (the largest coarse level, 8x fewer points than the fine one but 81-99
+    // pattern entries per row) skips the pre-smoothing: R_1 itself is restricted and
+    // Z_1 starts from the coarse correction.  The cycle is then not exactly
+    // symmetric; CG still takes it as a preconditioner (one iteration more at most on
+    // the benchmark cells, against one residual pass of level 1 less per cycle).
     for (int l = 1; l < L; ++l) {
         const int *pts = m.pts[l];
         const float *R = m.R[l];
         float *Z = m.Z[l], *T = m.T[l];
         const float ds = m.dscale;
-        for (int i = tid; i < m.n[l]; i += nt) {
-            const int o = pts[i];
-            Z[o] = ds * __ldg(m.dinv[l] + i) * R[o];
+        if (l > 1) {
+            for (int i = tid; i < m.n[l]; i += nt) {
+                const int o = pts[i];
+                Z[o] = ds * __ldg(m.dinv[l] + i) * R[o];
+            }
+            __syncthreads();
+            mg_resid(l, R, Z, T);
+            __syncthreads();
         }
-        __syncthreads();
-        mg_resid(l, R, Z, T);
-        __syncthreads();
-        mg_restrict(m, l, T, m.Bp1[l], m.Bp2[l], kMgPadDev);
+        mg_restrict(m, l, l > 1 ? T : R, m.Bp1[l], m.Bp2[l], kMgPadDev);
         __syncthreads();
     }
     // coarsest: z = A_L^-1 r, one warp per row
@@ -1299,7 +1306,7 @@ __device__ __noinline__ void mg_coarse_cycle()
             const int o = pts[i];
             int u0, u1, u2;
             mg_coords(o, m.Bp1[l], m.Bp2[l], u0, u1, u2);
-            Z[o] = ds * __ldg(m.dinv[l] + i) * R[o] +
+            Z[o] = (l > 1 ? ds * __ldg(m.dinv[l] + i) * R[o] : 0.f) +
                    mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
         }
         __syncthreads();

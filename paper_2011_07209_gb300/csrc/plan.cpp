@@ -908,7 +908,7 @@ std::vector<exx_schedule> schedule_candidates(bool mg, double omega_default)
 {
     std::vector<exx_schedule> c;
     if (mg)
-        for (float om : {0.7f, 0.6f, 0.8f})
+        for (float om : {0.8f, 0.7f, 0.6f})
             for (int sh : {14, 18}) c.push_back({EXX_PRECOND_MG, om, sh, 0.0});
     for (int sh : {14, 18}) c.push_back({EXX_PRECOND_NONE, (float)omega_default, sh, 0.0});
     return c;

@@ -140,7 +140,7 @@ struct MgTables {
 int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t);
 
 // Candidate schedules of the autotuner (exx_plan_autotune), in the order that
-// breaks ties: with a multigrid hierarchy, MG with omega 0.7, 0.6, 0.8, each
+// breaks ties: with a multigrid hierarchy, MG with omega 0.8, 0.7, 0.6, each
 // with inner_shift 14 then 18; then plain CG with inner_shift 14, 18.
 std::vector<exx_schedule> schedule_candidates(bool mg, double omega_default);
 // Longest-processing-time partition of n jobs over n_ranks: jobs in order of

@@ -236,7 +236,9 @@ struct MgT {
             }
             return;
         }
-        for (int i = 0; i < t.n[l]; ++i) z[t.pts[l][i]] = t.dinv[l][i] * r[t.pts[l][i]];
+        // level 1 skips the pre-smoothing (as the solver does): R_1 is restricted as is
+        if (l > 1)
+            for (int i = 0; i < t.n[l]; ++i) z[t.pts[l][i]] = t.dinv[l][i] * r[t.pts[l][i]];
         std::vector<float> y, tb(t.box[l], 0.f), rc, zc;
         apply(l, z, y);
         for (int i = 0; i < t.n[l]; ++i) tb[t.pts[l][i]] = r[t.pts[l][i]] - y[t.pts[l][i]];
@@ -350,7 +352,7 @@ int main(int argc, char **argv)
     const int k1 = pcg(A, b, &mg, 1e-9, x1);
     // the device tables of the same hierarchy, applied in FP32 as the solver does
     MgTables T;
-    if (make_mg_tables(L, st, 3, 200, 0.7, T)) return 5;
+    if (make_mg_tables(L, st, 3, 200, 0.8, T)) return 5;
     int k2 = -1, n_exp1 = 0;
     double rel2 = 1.0;
     if (T.nlev >= 2) {
@@ -358,7 +360,7 @@ int main(int argc, char **argv)
         make_mg_levels(L, st, 3, 200, lv2);
         MgT mt{&T, &lv2[0], 0.f};
         for (int k = lv2[0].row[0]; k < lv2[0].row[1]; ++k)
-            if (lv2[0].col[k] == 0) mt.c0 = (float)(0.7 / lv2[0].val[k]);
+            if (lv2[0].col[k] == 0) mt.c0 = (float)(0.8 / lv2[0].val[k]);
         Vec x2;
         k2 = pcg(A, b, &mt, 1e-9, x2);
         double d2 = 0.0, n2 = 0.0;

@@ -33,10 +33,10 @@ def _run(exe, mg, *ms):
 
 def test_candidates(harness):
     r = _run(harness, True)
-    # MG with omega 0.7, 0.6, 0.8 (inner_shift 14, 18 each), then plain CG
+    # MG with omega 0.8, 0.7, 0.6 (inner_shift 14, 18 each), then plain CG
     assert r["n"] == 8
-    assert r["cand"][0] == [1, 0.7, 14] and r["cand"][1] == [1, 0.7, 18]
-    assert [c[1] for c in r["cand"][:6:2]] == [0.7, 0.6, 0.8]
+    assert r["cand"][0] == [1, 0.8, 14] and r["cand"][1] == [1, 0.8, 18]
+    assert [c[1] for c in r["cand"][:6:2]] == [0.8, 0.7, 0.6]
     assert r["cand"][6] == [0, 0.7, 14] and r["cand"][7] == [0, 0.7, 18]
     plain = _run(harness, False)
     assert plain["n"] == 2 and all(c[0] == 0 for c in plain["cand"])

@@ -17,6 +17,10 @@ import paper_2011_07209_gb300.synth as synth
 pytestmark = pytest.mark.gpu
 
 E_TOL = {"fp64": 1e-9, "mixed": 1e-7}
+# per pair, relative to the pair's own E: the oracle and the GPU both stop at
+# |b - A v| <= tol |b| (tol 1e-10 here), which bounds each one's relative error in
+# int rho v by sqrt(cond A) tol ~ 6e-9; the mixed path adds its FP32 moments
+PAIR_TOL = {"fp64": 2e-8, "mixed": 1e-7}
 D_TOL = 1e-6
 PI_TOL = 1e-8
 
@@ -62,8 +66,10 @@ def _compare(g, o, precision, per_pair=True):
     assert g["e_xx"] == pytest.approx(o["e_xx"], rel=E_TOL[precision])
     assert np.abs(g["stress"] - o["stress"]).max() < PI_TOL
     if per_pair:
-        rel = np.abs(g["pair_e"] - o["pair_e"]) / np.abs(o["pair_e"]).max()
-        assert rel.max() < 10 * E_TOL[precision]
+        # every pair against its own value (not the cell's largest), so that a distant
+        # pair with a tiny E_pair is held to the same relative bound
+        rel = np.abs(g["pair_e"] - o["pair_e"]) / np.abs(o["pair_e"])
+        assert rel.max() < PAIR_TOL[precision], rel.max()
     if o["dxx"] is not None:
         assert np.abs(g["dxx"] - o["dxx"]).max() < D_TOL
 
