@@ -259,8 +259,20 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         v.off = off;
         off += 3 * v.stride;
         if ((e = mg_put(p, s, T.pts[l], &v.pts)) || (e = mg_put(p, s, T.wexp[l], &v.wexp)) ||
-            (e = mg_put(p, s, T.dinv[l], &v.dinv)) || (e = mg_put(p, s, T.dbox[l], &v.dbox)))
+            (e = mg_put(p, s, T.dinv[l], &v.dinv)) || (e = mg_put(p, s, T.dbox[l], &v.dbox)) ||
+            (e = mg_put(p, s, T.groups[l], &v.groups)))
             return e;
+        {
+            const int32_t *ge = nullptr;
+            if ((e = mg_put(p, s, T.gexp[l], &ge))) return e;
+            v.gexp = reinterpret_cast<const int4 *>(ge);
+        }
+        v.n_groups = (int)T.groups[l].size();
+        v.n_pure = T.n_pure[l];
+        for (int k = 0; k < 125; ++k) {
+            G.wdense[l][k] = T.wdense[l][k];
+            G.kmap[l][k] = T.kmap[l][k];
+        }
         for (int k = 0; k < T.K[l]; ++k) {
             G.kd[l][k] = T.kd[l][k];
             G.wint[l][k] = T.wint[l][k];

@@ -29,6 +29,9 @@ struct MgLevelDev {
     const float *wexp;             // [K][n_exp] weights of the non-interior rows, pattern-major
     const float *dinv;             // [n] omega / diag(A_l)
     const float *dbox;             // [box] the same on the padded box, zero at inactive points
+    int n_groups, n_pure;          // runs of 4 points along the last axis (Bp[2] % 4 == 0); the first
+    const int32_t *groups;         // n_pure hold interior rows only: (offset / 4) << 4 | mask
+    const int4 *gexp;              // [n_groups] row of wexp of each point, -1 interior or inactive
 };
 struct MgDev {
     int nlev;                      // levels including the fine one; 0: no hierarchy
@@ -37,6 +40,8 @@ struct MgDev {
     MgLevelDev lv[kMgLevelsDev];   // lv[1 .. nlev-1]
     int kd[kMgLevelsDev][kMgKDev]; // pattern offsets, (dx+2) | (dy+2) << 3 | (dz+2) << 6
     float wint[kMgLevelsDev][kMgKDev];
+    float wdense[kMgLevelsDev][125];   // interior weights on the 5 x 5 x 5 window ((dx+2) * 5 + dy+2) * 5 + dz+2
+    int kmap[kMgLevelsDev][125];       // window position -> pattern entry, -1 outside the pattern
     const float *cinv;             // [n][n] inverse of the coarsest operator, row-major
 };
 

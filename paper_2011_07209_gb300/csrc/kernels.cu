@@ -1096,6 +1096,11 @@ struct MgSm {                      // the hierarchy of the pair's set, in shared
     const float *cinv;
     int koff[kMgLevelsDev][kMgKDev];
     float wint[kMgLevelsDev][kMgKDev];
+    int n_groups[kMgLevelsDev], n_pure[kMgLevelsDev];
+    const int32_t *groups[kMgLevelsDev];
+    const int4 *gexp[kMgLevelsDev];
+    float wdense[125];             // the window weights and map of level 1 (the level of the run path)
+    int kmap[125];
     float cr[kMgCoarsestDev];
 };
 
@@ -1229,6 +1234,64 @@ __device__ __forceinline__ float mg_row(int l, int i, int o, const float *__rest
     return s0 + s1;
 }
 
+// T = R - A_l X on coarse level 1, by runs of 4 points along the last axis:
+// for each of the 25 (dx, dy) rows of the 5 x 5 x 5 window, three aligned float4
+// loads give the 12 values that the run's four points need (the same loads
+// serve all four), and the weights come from the interior stencil in shared
+// memory or, for points with rows of their own, from wexp.
+__device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const float *__restrict__ X,
+                                              float *__restrict__ T)
+{
+    const MgSm &m = g_mg_sm;
+    const int l = 1;
+    const int ng = m.n_groups[l], npure = m.n_pure[l];
+    const int B1 = m.Bp1[l], B2 = m.Bp2[l], ne = m.n_exp[l];
+    const float *__restrict__ wexp = m.wexp[l];
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int32_t gw = __ldg(m.groups[l] + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (g < npure) {
+#pragma unroll 1
+            for (int dxy = 0; dxy < 25; ++dxy) {
+                const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
+                const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
+                const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int dz = 0; dz < 5; ++dz) {
+                    const float w = m.wdense[dxy * 5 + dz];
+                    if (w == 0.f) continue;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] += w * x[2 + i + dz];
+                }
+            }
+        } else {
+            const int4 e4 = __ldg(m.gexp[l] + g);
+            const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll 1
+            for (int dxy = 0; dxy < 25; ++dxy) {
+                const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
+                const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
+                const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int dz = 0; dz < 5; ++dz) {
+                    const int k = m.kmap[dxy * 5 + dz];
+                    if (k < 0) continue;
+                    const float wi = m.wdense[dxy * 5 + dz];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float w = ev[i] < 0 ? wi : __ldg(wexp + (size_t)k * ne + ev[i]);
+                        acc[i] += w * x[2 + i + dz];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (mask & (1 << i)) T[off + i] = R[off + i] - acc[i];
+    }
+}
+
 // T = R - A_l X on the active points of coarse level l.  Levels with fewer
 // rows than half the CTA's threads give each row 2, 4 or 8 adjacent lanes,
 // which split the pattern and add their parts by shuffles.
@@ -1310,7 +1373,8 @@ __device__ __noinline__ void mg_coarse_cycle()
                    mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
         }
         __syncthreads();
-        mg_resid(l, R, Z, T);
+        if (l == 1 && m.n_groups[1] > 0) mg_resid_runs(R, Z, T);
+        else mg_resid(l, R, Z, T);
         __syncthreads();
         for (int i = tid; i < m.n[l]; i += nt) {
             const int o = pts[i];
@@ -1446,8 +1510,17 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                 m.wexp[l] = v.wexp;
                 m.dinv[l] = v.dinv;
                 m.dbox[l] = v.dbox;
+                m.n_groups[l] = v.n_groups;
+                m.n_pure[l] = v.n_pure;
+                m.groups[l] = v.groups;
+                m.gexp[l] = v.gexp;
             }
         }
+        if (G.nlev > 2)
+            for (int k = tid; k < 125; k += nt) {
+                m.wdense[k] = G.wdense[1][k];
+                m.kmap[k] = G.kmap[1][k];
+            }
         for (int l = 1; l < G.nlev; ++l)
             for (int k = tid; k < G.lv[l].K; k += nt) {
                 const int kd = G.kd[l][k];

@@ -778,6 +778,7 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
         const MgLevel &A = lv[l];
         r.n[l] = A.n;
         for (int a = 0; a < 3; ++a) r.Bp[l][a] = A.B[a] + 2 * kMgPad;
+        r.Bp[l][2] = (r.Bp[l][2] + 3) & ~3;   // rows start on 16-byte boundaries
         r.box[l] = (long long)r.Bp[l][0] * r.Bp[l][1] * r.Bp[l][2];
         r.slot_floats += 3 * ((r.box[l] + 63) & ~63LL);
         std::vector<int> u((size_t)3 * A.n);
@@ -891,6 +892,41 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
                 for (int k = 0; k < K; ++k) r.wexp[l][(size_t)k * n_exp + (q - n_int)] = (float)w[(size_t)i * K + k];
         }
         r.pts[l] = std::move(pts);
+        // dense interior stencil, window -> pattern map, and runs of 4 points
+        std::fill(r.kmap[l], r.kmap[l] + 125, -1);
+        for (int k = 0; k < K; ++k) {
+            const int kd = r.kd[l][k];
+            const int pos = ((kd & 7) * 5 + ((kd >> 3) & 7)) * 5 + ((kd >> 6) & 7);   // (dx, dy, dz) + 2
+            r.wdense[l][pos] = r.wint[l][k];
+            r.kmap[l][pos] = k;
+        }
+        std::vector<int32_t> at((size_t)r.box[l], -1);
+        for (int q = 0; q < A.n; ++q) at[(size_t)r.pts[l][q]] = q;
+        const long long rows = (long long)r.Bp[l][0] * r.Bp[l][1];
+        std::vector<int32_t> mixed_g, mixed_e;
+        for (long long row = 0; row < rows; ++row)
+            for (int g4 = 0; g4 < r.Bp[l][2] / 4; ++g4) {
+                const long long off = row * r.Bp[l][2] + 4 * g4;
+                int mask = 0, e4[4] = {-1, -1, -1, -1};
+                bool pure = true;
+                for (int i = 0; i < 4; ++i) {
+                    const int q = at[(size_t)(off + i)];
+                    if (q < 0) continue;
+                    mask |= 1 << i;
+                    if (q >= n_int) {
+                        pure = false;
+                        e4[i] = q - n_int;
+                    }
+                }
+                if (!mask) continue;
+                std::vector<int32_t> &G = pure ? r.groups[l] : mixed_g;
+                std::vector<int32_t> &E = pure ? r.gexp[l] : mixed_e;
+                G.push_back((int32_t)((off >> 2) << 4 | mask));
+                for (int i = 0; i < 4; ++i) E.push_back(e4[i]);
+            }
+        r.n_pure[l] = (int)r.groups[l].size();
+        r.groups[l].insert(r.groups[l].end(), mixed_g.begin(), mixed_g.end());
+        r.gexp[l].insert(r.gexp[l].end(), mixed_e.begin(), mixed_e.end());
     }
     t = std::move(r);
     return EXX_OK;

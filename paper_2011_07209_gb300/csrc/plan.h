@@ -134,6 +134,14 @@ struct MgTables {
     std::vector<float> wexp[kMgMaxLevels];          // [K][n_exp], n_exp = n - n_int
     std::vector<float> dinv[kMgMaxLevels];
     std::vector<float> dbox[kMgMaxLevels];          // dinv on the padded box
+    // for the residual pass: the active points as aligned runs of 4 along the last
+    // axis (the last axis of the padded box is a multiple of 4 long), each run as
+    // (offset / 4) << 4 | mask with the row of wexp of each of its 4 points (-1:
+    // interior or inactive); runs without explicit rows first
+    std::vector<int32_t> groups[kMgMaxLevels], gexp[kMgMaxLevels];   // gexp: [n_groups][4]
+    int n_pure[kMgMaxLevels] = {};                  // leading runs whose points are all interior
+    float wdense[kMgMaxLevels][125] = {};           // interior stencil on the 5 x 5 x 5 window (dx, dy, dz)
+    int kmap[kMgMaxLevels][125] = {};               // window position -> pattern entry k, -1 outside the pattern
     std::vector<float> cinv;                        // [n][n] of the coarsest level
     long long slot_floats = 0;                      // three boxes per coarse level
 };
