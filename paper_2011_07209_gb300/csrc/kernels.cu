@@ -494,18 +494,22 @@ __device__ __noinline__ void energy_stress_df(const SetDev &S, const float2 (*w1
         int m0, m1, m2;
         unpack_m(S.pe_m[k], m0, m1, m2);
         const float mf[3] = {(float)m0, (float)m1, (float)m2};
+        // the derivative in FP32 from the differences of the double-float values (hi
+        // and lo parts differenced separately): sigma needs about 1e-5 relative (its
+        // tolerance 1e-8 Ha/bohr^3 against |Pi| ~ 1e-3), FP32 gives about 1e-7; only
+        // the products with rho and the sums stay double-float
 #pragma unroll
         for (int db = 0; db < 3; ++db) {
             const int st = S.gstride[db];
-            float2 d = make_float2(0.f, 0.f);
+            float d_ = 0.f;
 #pragma unroll
             for (int s_ = 1; s_ <= 4; ++s_) {
                 if (s_ <= fdn) {
-                    const float2 vm = vb[off - s_ * st];
-                    d = dw_add(d, dw_mul(w1[db][s_], dw_add(vb[off + s_ * st], make_float2(-vm.x, -vm.y))));
+                    const float2 vp = vb[off + s_ * st], vm = vb[off - s_ * st];
+                    d_ += w1[db][s_].x * ((vp.x - vm.x) + (vp.y - vm.y));
                 }
             }
-            const float2 rd = dw_mul(b, d);   // 4 pi rho d_b v
+            const float2 rd = dw_mul(b, make_float2(d_, 0.f));   // 4 pi rho d_b v
 #pragma unroll
             for (int al = 0; al < 3; ++al) {
                 const float2 p = two_prod(mf[al], rd.x);   // m_alpha is an integer below 2^10: exact
@@ -1848,6 +1852,39 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
     }
 }
 
+// |b|^2 for b = 4 pi rho + L v with v zero on PE and the far field on the halo
+// (v as double-float pairs), the stencil in FP32 and the sum in double-float.
+// Only the stopping threshold tol |b| uses it when the CG starts from the
+// multipole guess, whose residual (double-float) is the CG's first residual.
+__device__ __noinline__ double bnorm2_f32(const SetDev &S, const float2 *__restrict__ vb,
+                                          const float2 *__restrict__ b2, const float (*cw)[8], float center,
+                                          const int *ds, int ndir, int fdn, float2 *red2)
+{
+    DF a[1] = {{0.f, 0.f}};
+    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        float acc = center * vb[off].x;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (d < ndir) {
+                const int st = ds[d];
+#pragma unroll
+                for (int s_ = 1; s_ <= 6; ++s_)
+                    if (s_ <= fdn) acc += cw[d][s_] * (vb[off + s_ * st].x + vb[off - s_ * st].x);
+            }
+        }
+        const float2 q = b2[k];
+        const float b = (q.x + acc) + q.y;
+        df_fma(a[0], b, b);
+    }
+    block_sum_df<1>(a, red2);
+    // block_sum_df leaves the total in warp 0: broadcast it
+    __shared__ double s_bn2;
+    if (threadIdx.x == 0) s_bn2 = (double)a[0].hi + (double)a[0].lo;
+    __syncthreads();
+    return s_bn2;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(const CellDev *__restrict__ cells, ListDev L,
                                                                  SlotWork W, int inner_shift)
@@ -2026,8 +2063,12 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         __syncthreads();
 
         // ---- Step IV: Poisson solve (Eq. pe) ----
-        // b = 4 pi rho + (Dirichlet terms): the residual of v = 0 on PE
-        double rr2 = residual();
+        // b = 4 pi rho + (Dirichlet terms): the residual of v = 0 on PE.  When the CG
+        // will start from the multipole guess (no warm start), only |b| is needed here
+        const bool b_only = dfm && C.guess && S.gs_perm && !C.warm_map;
+        double rr2 = b_only ? bnorm2_f32(S, vb, b2, sm.cw32, sm.center32, sm.ds, ndir, fdn,
+                                         reinterpret_cast<float2 *>(red))
+                            : residual();
         const double bn = sqrt(rr2);
         const double stop = C.tol * bn;
         int iters = 0, refine = 1, status = 0;
