@@ -1200,13 +1200,7 @@ __device__ __forceinline__ float mg_prolong_at(const MgSm &m, int l, int u0, int
     return w0 * w1 * s;
 }
 
-struct MgScalars {
-    double rz, rmax, S;
-    float alpha, beta;
-    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
-};
 __shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid path
-__shared__ MgScalars g_mg_cs;
 
 // Part of (A_l x) at active point i (box offset o) of coarse level l: the
 // pattern entries k = sub, sub + tpr, ... (tpr threads share a row on the small
@@ -1388,85 +1382,46 @@ __device__ __noinline__ void mg_coarse_cycle()
     }
 }
 
-// z = M r on the fine level: r in rf, z written to zout (dense boxes, zero
-// outside PE); zf holds the smoothed part z0.  Returns <r, z> (valid in warp 0).
-template <int FDN>
-__device__ __forceinline__ double mg_precondition(const CgMixed &cg, const MgSm &m, const float *__restrict__ rf,
-                                                  float *__restrict__ zf, float *__restrict__ zout)
+// One pass over the aligned groups that runs a pointwise update ahead of a
+// stencil: groups are sorted by box offset, so the stencil of chunk c (W groups)
+// reads only groups below need[c] (the chunk's last offset plus the stencil
+// reach); the update front is brought to need[c] before the chunk's stencil,
+// with one CTA barrier per chunk.  The stencil then reads the updated vector
+// while it is still cache-resident, and every group is updated exactly once.
+template <class Upd, class Sten>
+__device__ __forceinline__ void front_sweep(int ng, int nchunk, int W, const int *need, Upd upd, Sten sten)
 {
-    const SetDev &S = *cg.S;
-    const SmemCell &sm = *cg.sm;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int32_t *__restrict__ grp = S.groups;
-    const int ng = S.n_groups, ndir = cg.ndir;
-    const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
-    const float(*cw)[8] = sm.cw32;
-    const float center = sm.center32, c0 = m.c0;
-    const int B1 = S.B[1], B2 = S.B[2];
-    // pre-smoothed residual t = r - c0 A r = r + c0 L r, into zout
-    for (int g = tid; g < ng; g += nt) {
-        const int32_t gw = __ldg(grp + g);
-        const int off = (gw >> 4) << 2, mask = gw & 15;
-        float acc[4];
-        lap_group<FDN>(rf, off, cw, center, rs, dsf, d2, ndir, acc);
-        const float4 r = ld4(rf + off);
-        st4(zout + off, (mask & 1) ? r.x + c0 * acc[0] : 0.f, (mask & 2) ? r.y + c0 * acc[1] : 0.f,
-            (mask & 4) ? r.z + c0 * acc[2] : 0.f, (mask & 8) ? r.w + c0 * acc[3] : 0.f);
-    }
-    __syncthreads();
-    mg_restrict(m, 0, zout, B1, B2, 0);
-    __syncthreads();
-    mg_coarse_cycle();
-    // z0 = c0 r + P Z_1 on PE.  The group's four points u2 .. u2+3 (u2 even, a
-    // multiple of 4) take their last-axis parents from the three level-1 values
-    // at u2/2, u2/2 + 1, u2/2 + 2 of each (x, y) parent row.
-    {
-        const float *Z1 = m.Z[1];
-        const int cB1 = m.Bp1[1], cB2 = m.Bp2[1];
-        for (int g = tid; g < ng; g += nt) {
-            const int32_t gw = __ldg(grp + g);
-            const int off = (gw >> 4) << 2, mask = gw & 15;
-            int u0, u1, u2;
-            mg_coords(off, B1, B2, u0, u1, u2);
-            const int a0 = u0 >> 1, a1 = u1 >> 1, n0 = (u0 & 1) + 1, n1 = (u1 & 1) + 1;
-            float c_0 = 0.f, c_1 = 0.f, c_2 = 0.f;
-            for (int x = 0; x < n0; ++x)
-                for (int y = 0; y < n1; ++y) {
-                    const float *row =
-                        Z1 + ((size_t)(a0 + x + kMgPadDev) * cB1 + (a1 + y + kMgPadDev)) * cB2 + (u2 >> 1) + kMgPadDev;
-                    c_0 += row[0];
-                    c_1 += row[1];
-                    c_2 += row[2];
-                }
-            const float wxy = (n0 == 2 ? 0.5f : 1.f) * (n1 == 2 ? 0.5f : 1.f);
-            const float4 r = ld4(rf + off);
-            st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f, (mask & 2) ? c0 * r.y + wxy * 0.5f * (c_0 + c_1) : 0.f,
-                (mask & 4) ? c0 * r.z + wxy * c_1 : 0.f, (mask & 8) ? c0 * r.w + wxy * 0.5f * (c_1 + c_2) : 0.f);
+    int front = 0;
+    for (int c = 0; c < nchunk; ++c) {
+        for (const int nd = need[c]; front < nd; front += nt) {
+            const int g = front + tid;
+            if (g < ng) upd(g);
         }
+        __syncthreads();
+        const int gend = min(ng, (c + 1) * W);
+        for (int g = c * W + tid; g < gend; g += nt) sten(g);
     }
-    __syncthreads();
-    // z = z0 + c0 (r - A z0) = z0 + c0 (r + L z0), and <r, z>
-    DF a[1] = {{0.f, 0.f}};
-    for (int g = tid; g < ng; g += nt) {
-        const int32_t gw = __ldg(grp + g);
-        const int off = (gw >> 4) << 2, mask = gw & 15;
-        float acc[4];
-        lap_group<FDN>(zf, off, cw, center, rs, dsf, d2, ndir, acc);
-        const float4 r = ld4(rf + off), z0 = ld4(zf + off);
-        const float z_0 = (mask & 1) ? z0.x + c0 * (r.x + acc[0]) : 0.f;
-        const float z_1 = (mask & 2) ? z0.y + c0 * (r.y + acc[1]) : 0.f;
-        const float z_2 = (mask & 4) ? z0.z + c0 * (r.z + acc[2]) : 0.f;
-        const float z_3 = (mask & 8) ? z0.w + c0 * (r.w + acc[3]) : 0.f;
-        st4(zout + off, z_0, z_1, z_2, z_3);
-        df_add(a[0], r.x * z_0 + r.y * z_1 + r.z * z_2 + r.w * z_3);
-    }
-    block_sum_df<1>(a, reinterpret_cast<float2 *>(cg.red));
-    return (double)a[0].hi + (double)a[0].lo;
 }
+
+__shared__ int g_mg_need[kMaxSweepChunks];   // update front of each chunk (multigrid path)
+
+struct MgScalars {
+    double rz, rmax, S;
+    float alpha, beta;
+    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+};
+__shared__ MgScalars g_mg_cs;
 
 // The mixed-precision solve of one pair with the multigrid preconditioner (see
 // the comment above MgSm).  zf: one more dense FP32 box; mgbase: the slot's
-// region for the coarse boxes.
+// region for the coarse boxes.  One PCG iteration is four passes over the fine
+// groups, each a pointwise update run ahead of a stencil (front_sweep):
+//   A  p = z + beta p           ahead of   q = A p, <p, q>
+//   B  r -= alpha q, e += alpha p   ahead of   t = r + c0 L r (pre-smoothed residual)
+//      restriction of t, the coarse levels
+//   D  z0 = c0 r + P Z_1         ahead of   z = z0 + c0 (r + L z0), <r, z>
+// (pass B's t is discarded when its <r, r> calls for a reliable update).
 template <int FDN>
 __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mgbase, int &iters, int &refine,
                                          int &status, double &rnorm)
@@ -1488,6 +1443,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
     const float center = sm.center32;
     const double stop = cg.stop, inner_red = cg.inner_red;
     float2 *red2 = reinterpret_cast<float2 *>(cg.red);
+    const int B1 = S.B[1], B2 = S.B[2];
 
     MgSm &m = g_mg_sm;
     MgScalars &cs = g_mg_cs;
@@ -1535,9 +1491,90 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
         // the coarse boxes start all zero: points that are inactive for this set
         // are read by the restriction and must hold zeros
         for (long long k = tid; k < G.floats; k += nt) mgbase[k] = 0.f;
-        __syncthreads();
     }
+    // update front of every chunk of the fused passes
+    const int W = kSweepChunkGroups * nt;
+    const int nchunk = (ng + W - 1) / W;
+    {
+        int reach = 7;
+        for (int d = 0; d < ndir; ++d) reach = max(reach, 3 + FDN * max(abs(dsf[d]), abs(rs[d])));
+        for (int c = tid; c < nchunk; c += nt) {
+            const int last = min(ng, (c + 1) * W) - 1;
+            const long long lim = (long long)((grp[last] >> 4) << 2) + reach;
+            int lo = last + 1, hi = ng;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)((grp[mid] >> 4) << 2) <= lim) lo = mid + 1;
+                else hi = mid;
+            }
+            g_mg_need[c] = lo;
+        }
+    }
+    __syncthreads();
     if (!(cg.r0n > stop)) return;   // the starting guess already meets the tolerance
+    const float c0 = m.c0;
+
+    // the stencil half of pass B: t = r + c0 L r into qf
+    auto pre_smooth = [&](int g) {
+        const int32_t gw = __ldg(grp + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        float acc[4];
+        lap_group<FDN>(rf, off, cw, center, rs, dsf, d2, ndir, acc);
+        const float4 r = ld4(rf + off);
+        st4(qf + off, (mask & 1) ? r.x + c0 * acc[0] : 0.f, (mask & 2) ? r.y + c0 * acc[1] : 0.f,
+            (mask & 4) ? r.z + c0 * acc[2] : 0.f, (mask & 8) ? r.w + c0 * acc[3] : 0.f);
+    };
+    // restriction, coarse levels and pass D: z into qf, <r, z> returned (valid in warp 0)
+    auto finish_precondition = [&]() -> double {
+        __syncthreads();
+        mg_restrict(m, 0, qf, B1, B2, 0);
+        __syncthreads();
+        mg_coarse_cycle();
+        const float *Z1 = m.Z[1];
+        const int cB1 = m.Bp1[1], cB2 = m.Bp2[1];
+        DF a[1] = {{0.f, 0.f}};
+        front_sweep(
+            ng, nchunk, W, g_mg_need,
+            [&](int g) {
+                // z0 = c0 r + P Z_1: the group's four points u2 .. u2+3 (u2 a multiple of 4)
+                // take their last-axis parents from three level-1 values of each (x, y) row
+                const int32_t gw = __ldg(grp + g);
+                const int off = (gw >> 4) << 2, mask = gw & 15;
+                int u0, u1, u2;
+                mg_coords(off, B1, B2, u0, u1, u2);
+                const int a0 = u0 >> 1, a1 = u1 >> 1, n0 = (u0 & 1) + 1, n1 = (u1 & 1) + 1;
+                float c_0 = 0.f, c_1 = 0.f, c_2 = 0.f;
+                for (int x = 0; x < n0; ++x)
+                    for (int y = 0; y < n1; ++y) {
+                        const float *row = Z1 + ((size_t)(a0 + x + kMgPadDev) * cB1 + (a1 + y + kMgPadDev)) * cB2 +
+                                           (u2 >> 1) + kMgPadDev;
+                        c_0 += row[0];
+                        c_1 += row[1];
+                        c_2 += row[2];
+                    }
+                const float wxy = (n0 == 2 ? 0.5f : 1.f) * (n1 == 2 ? 0.5f : 1.f);
+                const float4 r = ld4(rf + off);
+                st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f,
+                    (mask & 2) ? c0 * r.y + wxy * 0.5f * (c_0 + c_1) : 0.f, (mask & 4) ? c0 * r.z + wxy * c_1 : 0.f,
+                    (mask & 8) ? c0 * r.w + wxy * 0.5f * (c_1 + c_2) : 0.f);
+            },
+            [&](int g) {
+                // z = z0 + c0 (r - A z0) = z0 + c0 (r + L z0)
+                const int32_t gw = __ldg(grp + g);
+                const int off = (gw >> 4) << 2, mask = gw & 15;
+                float acc[4];
+                lap_group<FDN>(zf, off, cw, center, rs, dsf, d2, ndir, acc);
+                const float4 r = ld4(rf + off), z0 = ld4(zf + off);
+                const float z_0 = (mask & 1) ? z0.x + c0 * (r.x + acc[0]) : 0.f;
+                const float z_1 = (mask & 2) ? z0.y + c0 * (r.y + acc[1]) : 0.f;
+                const float z_2 = (mask & 4) ? z0.z + c0 * (r.z + acc[2]) : 0.f;
+                const float z_3 = (mask & 8) ? z0.w + c0 * (r.w + acc[3]) : 0.f;
+                st4(qf + off, z_0, z_1, z_2, z_3);
+                df_add(a[0], r.x * z_0 + r.y * z_1 + r.z * z_2 + r.w * z_3);
+            });
+        block_sum_df<1>(a, red2);
+        return (double)a[0].hi + (double)a[0].lo;
+    };
 
     // frame of the starting residual (r32 holds the last true residual in FP32)
     double Sc = cg.r0n;
@@ -1556,36 +1593,50 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             if (tid == 0) cs.rmax = sqrt((double)a[0].hi + (double)a[0].lo);
             __syncthreads();
         }
-        const double rz0 = mg_precondition<FDN>(cg, m, rf, zf, qf);
+        // z = M r from the frame's residual (pass B without its update)
+        for (int g = tid; g < ng; g += nt) pre_smooth(g);
+        const double rz0 = finish_precondition();
         if (tid == 0) {
             cs.rz = rz0;
             cs.S = Sc;
+            cs.beta = 0.f;
         }
         __syncthreads();
-        for (int g = tid; g < ng; g += nt) {   // p = z
-            const int off = (__ldg(grp + g) >> 4) << 2;
-            *reinterpret_cast<float4 *>(pf + off) = ld4(qf + off);
-        }
-        __syncthreads();
+        bool first = true;   // p = z (no previous direction in this frame)
         bool restart = false;
         while (!restart) {
             if (iters >= cg.max_iter) {
                 status = 5;
                 return;
             }
-            // q = A p, <p, q>
+            // pass A: p = z + beta p ahead of q = A p, <p, q>
+            const float beta = cs.beta;
+            const bool copy = first;
+            first = false;
             DF a[1] = {{0.f, 0.f}};
-            for (int g = tid; g < ng; g += nt) {
-                const int32_t gw = __ldg(grp + g);
-                const int off = (gw >> 4) << 2, mask = gw & 15;
-                float acc[4];
-                lap_group<FDN>(pf, off, cw, center, rs, dsf, d2, ndir, acc);
-                const float4 p = ld4(pf + off);
-                const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
-                const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
-                st4(qf + off, q0, q1, q2, q3);
-                df_add(a[0], p.x * q0 + p.y * q1 + p.z * q2 + p.w * q3);
-            }
+            front_sweep(
+                ng, nchunk, W, g_mg_need,
+                [&](int g) {
+                    const int off = (__ldg(grp + g) >> 4) << 2;
+                    const float4 z = ld4(qf + off);
+                    if (copy) {
+                        *reinterpret_cast<float4 *>(pf + off) = z;
+                    } else {
+                        const float4 p = ld4(pf + off);
+                        st4(pf + off, z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w);
+                    }
+                },
+                [&](int g) {
+                    const int32_t gw = __ldg(grp + g);
+                    const int off = (gw >> 4) << 2, mask = gw & 15;
+                    float acc[4];
+                    lap_group<FDN>(pf, off, cw, center, rs, dsf, d2, ndir, acc);
+                    const float4 p = ld4(pf + off);
+                    const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
+                    const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
+                    st4(qf + off, q0, q1, q2, q3);
+                    df_add(a[0], p.x * q0 + p.y * q1 + p.z * q2 + p.w * q3);
+                });
             block_sum_df<1>(a, red2);
             if (tid == 0) {
                 const double pq = (double)a[0].hi + (double)a[0].lo;
@@ -1597,17 +1648,20 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             const float alpha = cs.alpha;
             int act = cs.act;
             if (!act) {
-                // e += alpha p, r -= alpha q, <r, r>
+                // pass B: e += alpha p, r -= alpha q (<r, r>) ahead of t = r + c0 L r
                 DF b[1] = {{0.f, 0.f}};
-                for (int g = tid; g < ng; g += nt) {
-                    const int off = (__ldg(grp + g) >> 4) << 2;
-                    const float4 r = ld4(rf + off), q = ld4(qf + off), p = ld4(pf + off), e = ld4(ef + off);
-                    const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z,
-                                r3 = r.w - alpha * q.w;
-                    st4(rf + off, r0, r1, r2, r3);
-                    st4(ef + off, e.x + alpha * p.x, e.y + alpha * p.y, e.z + alpha * p.z, e.w + alpha * p.w);
-                    df_add(b[0], r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-                }
+                front_sweep(
+                    ng, nchunk, W, g_mg_need,
+                    [&](int g) {
+                        const int off = (__ldg(grp + g) >> 4) << 2;
+                        const float4 r = ld4(rf + off), q = ld4(qf + off), p = ld4(pf + off), e = ld4(ef + off);
+                        const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z,
+                                    r3 = r.w - alpha * q.w;
+                        st4(rf + off, r0, r1, r2, r3);
+                        st4(ef + off, e.x + alpha * p.x, e.y + alpha * p.y, e.z + alpha * p.z, e.w + alpha * p.w);
+                        df_add(b[0], r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+                    },
+                    pre_smooth);
                 block_sum_df<1>(b, red2);
                 if (tid == 0) {
                     const double rr = (double)b[0].hi + (double)b[0].lo;
@@ -1638,18 +1692,11 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                 restart = true;
                 continue;
             }
-            // z = M r, beta = <r, z> / <r, z>_old, p = z + beta p
-            const double rz = mg_precondition<FDN>(cg, m, rf, zf, qf);
+            // the rest of z = M r (t is in qf), beta = <r, z> / <r, z>_old
+            const double rz = finish_precondition();
             if (tid == 0) {
                 cs.beta = (float)(rz / cs.rz);
                 cs.rz = rz;
-            }
-            __syncthreads();
-            const float beta = cs.beta;
-            for (int g = tid; g < ng; g += nt) {
-                const int off = (__ldg(grp + g) >> 4) << 2;
-                const float4 z = ld4(qf + off), p = ld4(pf + off);
-                st4(pf + off, z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w);
             }
             __syncthreads();
         }

