@@ -263,9 +263,9 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
             (e = mg_put(p, s, T.groups[l], &v.groups)))
             return e;
         {
-            const int32_t *ge = nullptr;
-            if ((e = mg_put(p, s, T.gexp[l], &ge))) return e;
-            v.gexp = reinterpret_cast<const int4 *>(ge);
+            const float *wm = nullptr;
+            if ((e = mg_put(p, s, T.wmix[l], &wm))) return e;
+            v.wmix = reinterpret_cast<const float4 *>(wm);
         }
         v.n_groups = (int)T.groups[l].size();
         v.n_pure = T.n_pure[l];
@@ -279,7 +279,7 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         }
     }
     G.floats = off;
-    if ((e = mg_put(p, s, T.cinv, &G.cinv))) return e;
+    if ((e = mg_put(p, s, T.cinv, &G.cinv)) || (e = mg_put(p, s, T.pinfo, &G.pinfo))) return e;
     if ((e = dev_alloc(&p->d_mg[s], 1))) return e;
     CK(cudaMemcpy(p->d_mg[s], &G, sizeof(MgDev), cudaMemcpyHostToDevice));
     return EXX_OK;

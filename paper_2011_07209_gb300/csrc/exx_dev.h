@@ -31,7 +31,7 @@ struct MgLevelDev {
     const float *dbox;             // [box] the same on the padded box, zero at inactive points
     int n_groups, n_pure;          // runs of 4 points along the last axis (Bp[2] % 4 == 0); the first
     const int32_t *groups;         // n_pure hold interior rows only: (offset / 4) << 4 | mask
-    const int4 *gexp;              // [n_groups] row of wexp of each point, -1 interior or inactive
+    const float4 *wmix;            // [125][n_groups - n_pure] weights of the other runs by window position
 };
 struct MgDev {
     int nlev;                      // levels including the fine one; 0: no hierarchy
@@ -43,6 +43,7 @@ struct MgDev {
     float wdense[kMgLevelsDev][125];   // interior weights on the 5 x 5 x 5 window ((dx+2) * 5 + dy+2) * 5 + dz+2
     int kmap[kMgLevelsDev][125];       // window position -> pattern entry, -1 outside the pattern
     const float *cinv;             // [n][n] inverse of the coarsest operator, row-major
+    const int32_t *pinfo;          // [fine groups] level-1 parents row << 2 | (u0 & 1) << 1 | (u1 & 1)
 };
 
 // Geometry of one subdomain kind (self pairs or non-self pairs) of one cell.

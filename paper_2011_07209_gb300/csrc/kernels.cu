@@ -779,22 +779,24 @@ __device__ __forceinline__ void st4s(float *p, float a, float b, float c, float 
 #endif
 }
 
-// q = -(L p) on the PE lanes of one aligned group (zero on the others), stored,
-// with the four products <p,q>, <q,q>, <r,q>, <r,p> of the group added to the
-// double-float dot accumulators.
+// (L f) at the four points off .. off+3 of one aligned group (off a multiple of
+// 4) into acc; returns f there.  The contiguous axis (d == 2) comes from the
+// group and its two neighbours.  A direction with no step along the contiguous
+// axis moves by rs[d], a multiple of 4, and reads whole groups.  A direction
+// with a step d2[d] = +-1 along it lands s_ d2[d] points off the group
+// boundary at the s_-th neighbour: the two aligned groups around that point
+// hold all four values, picked by compile-time indices (the sign of d2[d] is
+// the same for every thread).  Each group read holds at least one of the
+// values needed, so no read leaves the box.  Longer steps along the contiguous
+// axis read point by point.
 template <int FDN>
-__device__ __forceinline__ void stencil_group(const float *__restrict__ pf, const float *__restrict__ rf,
-                                              float *__restrict__ qf, int32_t gw, const float (*cw)[8], float center,
-                                              const int *rs, const int *dsf, const int *d2, int ndir, DF &apq, DF &aqq,
-                                              DF &arq, DF &arp)
+__device__ __forceinline__ float4 lap4(const float *__restrict__ x_, int off, const float (*cw)[8], float center,
+                                       const int *rs, const int *d2, int ndir, float (&acc)[4])
 {
-    const int off = (gw >> 4) << 2;
-    const int mask = gw & 15;
-    const float4 c = ld4(pf + off);
-    const float4 cm = ld4(pf + off - 4);
-    const float4 cp = ld4(pf + off + 4);
+    const float4 c = ld4(x_ + off);
+    const float4 cm = ld4(x_ + off - 4);
+    const float4 cp = ld4(x_ + off + 4);
     const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
-    float acc[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
 #pragma unroll
@@ -807,20 +809,61 @@ __device__ __forceinline__ void stencil_group(const float *__restrict__ pf, cons
         if (d2[d] == 0) {
 #pragma unroll
             for (int s_ = 1; s_ <= FDN; ++s_) {
-                const float4 a = ld4(pf + off + s_ * rs[d]);
-                const float4 b = ld4(pf + off - s_ * rs[d]);
+                const float4 a = ld4(x_ + off + s_ * rs[d]);
+                const float4 b = ld4(x_ + off - s_ * rs[d]);
                 acc[0] += cw[d][s_] * (a.x + b.x);
                 acc[1] += cw[d][s_] * (a.y + b.y);
                 acc[2] += cw[d][s_] * (a.z + b.z);
                 acc[3] += cw[d][s_] * (a.w + b.w);
             }
+        } else if (d2[d] == 1 || d2[d] == -1) {
+            // f(off + i + s_ dsf) = f(bp + i + s_ d2) and f(off + i - s_ dsf) = f(bm + i - s_ d2)
+            // with bp, bm = off +- s_ rs[d] on group boundaries
+            const bool up = d2[d] > 0;
+#pragma unroll
+            for (int s_ = 1; s_ <= FDN; ++s_) {
+                const int bp = off + s_ * rs[d], bm = off - s_ * rs[d];
+                if (up) {
+                    const float4 p0 = ld4(x_ + bp), p1 = ld4(x_ + bp + 4);   // bp .. bp+7
+                    const float4 m0 = ld4(x_ + bm - 4), m1 = ld4(x_ + bm);   // bm-4 .. bm+3
+                    const float P[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                    const float M[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (P[i + s_] + M[4 + i - s_]);
+                } else {
+                    const float4 p0 = ld4(x_ + bp - 4), p1 = ld4(x_ + bp);   // bp-4 .. bp+3
+                    const float4 m0 = ld4(x_ + bm), m1 = ld4(x_ + bm + 4);   // bm .. bm+7
+                    const float P[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                    const float M[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (P[4 + i - s_] + M[i + s_]);
+                }
+            }
         } else {
+            // longer steps along the contiguous axis (auxiliary directions beyond the first shell)
+            const int ds = rs[d] + d2[d];
 #pragma unroll
             for (int s_ = 1; s_ <= FDN; ++s_)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (pf[off + i + s_ * dsf[d]] + pf[off + i - s_ * dsf[d]]);
+                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (x_[off + i + s_ * ds] + x_[off + i - s_ * ds]);
         }
     }
+    return c;
+}
+
+// q = -(L p) on the PE lanes of one aligned group (zero on the others), stored,
+// with the four products <p,q>, <q,q>, <r,q>, <r,p> of the group added to the
+// double-float dot accumulators.
+template <int FDN>
+__device__ __forceinline__ void stencil_group(const float *__restrict__ pf, const float *__restrict__ rf,
+                                              float *__restrict__ qf, int32_t gw, const float (*cw)[8], float center,
+                                              const int *rs, const int *dsf, const int *d2, int ndir, DF &apq, DF &aqq,
+                                              DF &arq, DF &arp)
+{
+    const int off = (gw >> 4) << 2;
+    const int mask = gw & 15;
+    float acc[4];
+    const float4 c = lap4<FDN>(pf, off, cw, center, rs, d2, ndir, acc);
     const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
     const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
     st4s(qf + off, q0, q1, q2, q3);
@@ -1098,11 +1141,12 @@ struct MgSm {                      // the hierarchy of the pair's set, in shared
     const int32_t *pts[kMgLevelsDev];
     const float *wexp[kMgLevelsDev], *dinv[kMgLevelsDev], *dbox[kMgLevelsDev];
     const float *cinv;
+    const int32_t *pinfo;
     int koff[kMgLevelsDev][kMgKDev];
     float wint[kMgLevelsDev][kMgKDev];
     int n_groups[kMgLevelsDev], n_pure[kMgLevelsDev];
     const int32_t *groups[kMgLevelsDev];
-    const int4 *gexp[kMgLevelsDev];
+    const float4 *wmix[kMgLevelsDev];
     float wdense[125];             // the window weights and map of level 1 (the level of the run path)
     int kmap[125];
     float cr[kMgCoarsestDev];
@@ -1113,36 +1157,8 @@ template <int FDN>
 __device__ __forceinline__ void lap_group(const float *__restrict__ x_, int off, const float (*cw)[8], float center,
                                           const int *rs, const int *dsf, const int *d2, int ndir, float (&acc)[4])
 {
-    const float4 c = ld4(x_ + off);
-    const float4 cm = ld4(x_ + off - 4);
-    const float4 cp = ld4(x_ + off + 4);
-    const float x[12] = {cm.x, cm.y, cm.z, cm.w, c.x, c.y, c.z, c.w, cp.x, cp.y, cp.z, cp.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] = center * x[4 + i];
-#pragma unroll
-    for (int s_ = 1; s_ <= FDN; ++s_)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] += cw[2][s_] * (x[4 + i + s_] + x[4 + i - s_]);
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-        if (d == 2 || d >= ndir) continue;
-        if (d2[d] == 0) {
-#pragma unroll
-            for (int s_ = 1; s_ <= FDN; ++s_) {
-                const float4 a = ld4(x_ + off + s_ * rs[d]);
-                const float4 b = ld4(x_ + off - s_ * rs[d]);
-                acc[0] += cw[d][s_] * (a.x + b.x);
-                acc[1] += cw[d][s_] * (a.y + b.y);
-                acc[2] += cw[d][s_] * (a.z + b.z);
-                acc[3] += cw[d][s_] * (a.w + b.w);
-            }
-        } else {
-#pragma unroll
-            for (int s_ = 1; s_ <= FDN; ++s_)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] += cw[d][s_] * (x_[off + i + s_ * dsf[d]] + x_[off + i - s_ * dsf[d]]);
-        }
-    }
+    (void)dsf;
+    lap4<FDN>(x_, off, cw, center, rs, d2, ndir, acc);
 }
 
 __device__ __forceinline__ void mg_coords(int o, int B1, int B2, int &u0, int &u1, int &u2)
@@ -1236,15 +1252,14 @@ __device__ __forceinline__ float mg_row(int l, int i, int o, const float *__rest
 // for each of the 25 (dx, dy) rows of the 5 x 5 x 5 window, three aligned float4
 // loads give the 12 values that the run's four points need (the same loads
 // serve all four), and the weights come from the interior stencil in shared
-// memory or, for points with rows of their own, from wexp.
+// memory or, for runs with rows of their own, one float4 per window position.
 __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const float *__restrict__ X,
                                               float *__restrict__ T)
 {
     const MgSm &m = g_mg_sm;
     const int l = 1;
     const int ng = m.n_groups[l], npure = m.n_pure[l];
-    const int B1 = m.Bp1[l], B2 = m.Bp2[l], ne = m.n_exp[l];
-    const float *__restrict__ wexp = m.wexp[l];
+    const int B1 = m.Bp1[l], B2 = m.Bp2[l];
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
         const int32_t gw = __ldg(m.groups[l] + g);
         const int off = (gw >> 4) << 2, mask = gw & 15;
@@ -1264,8 +1279,9 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
                 }
             }
         } else {
-            const int4 e4 = __ldg(m.gexp[l] + g);
-            const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
+            // one float4 of weights per window position for the run's four points
+            const int nm = ng - npure;
+            const float4 *__restrict__ wm = m.wmix[l] + (g - npure);
 #pragma unroll 1
             for (int dxy = 0; dxy < 25; ++dxy) {
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
@@ -1273,20 +1289,55 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
                 const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 #pragma unroll
                 for (int dz = 0; dz < 5; ++dz) {
-                    const int k = m.kmap[dxy * 5 + dz];
-                    if (k < 0) continue;
-                    const float wi = m.wdense[dxy * 5 + dz];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float w = ev[i] < 0 ? wi : __ldg(wexp + (size_t)k * ne + ev[i]);
-                        acc[i] += w * x[2 + i + dz];
-                    }
+                    if (m.kmap[dxy * 5 + dz] < 0) continue;
+                    const float4 w = __ldg(wm + (size_t)(dxy * 5 + dz) * nm);
+                    acc[0] += w.x * x[2 + dz];
+                    acc[1] += w.y * x[3 + dz];
+                    acc[2] += w.z * x[4 + dz];
+                    acc[3] += w.w * x[5 + dz];
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (mask & (1 << i)) T[off + i] = R[off + i] - acc[i];
+    }
+}
+
+// R_1 = P^T t from the fine CG box t (B1, B2, no margin) by runs of 4 level-1
+// points along the last axis: their fine centres 2 c2 .. 2 c2 + 6 sit at a
+// multiple of 4 (level-1 runs start at u2 = 0 mod 4 with a margin of 2), so
+// three aligned float4 loads per fine (dx, dy) row give the nine values
+// 2 c2 - 1 .. 2 c2 + 7 that the four points need.  Same weights and order of
+// additions as mg_restrict.
+__device__ __forceinline__ void mg_restrict_runs(const float *__restrict__ src, int B1, int B2)
+{
+    const MgSm &m = g_mg_sm;
+    const int ng = m.n_groups[1];
+    float *__restrict__ dst = m.R[1];
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int32_t gw = __ldg(m.groups[1] + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        int c0, c1, c2;
+        mg_coords(off, m.Bp1[1], m.Bp2[1], c0, c1, c2);
+        c0 -= kMgPadDev;
+        c1 -= kMgPadDev;
+        c2 -= kMgPadDev;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const float *row = src + ((size_t)(2 * c0 + dx) * B1 + (2 * c1 + dy)) * B2 + 2 * c2;
+                const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
+                const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+                const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += w * (x[4 + 2 * i] + 0.5f * (x[3 + 2 * i] + x[5 + 2 * i]));
+            }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (mask & (1 << i)) dst[off + i] = acc[i];
     }
 }
 
@@ -1455,6 +1506,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             m.c0 = (float)(om / -(double)sm.center64);
             m.dscale = (float)(om / (double)G.omega);
             m.cinv = G.cinv;
+            m.pinfo = G.pinfo;
             for (int l = 1; l < G.nlev; ++l) {
                 const MgLevelDev &v = G.lv[l];
                 m.n[l] = v.n;
@@ -1473,7 +1525,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                 m.n_groups[l] = v.n_groups;
                 m.n_pure[l] = v.n_pure;
                 m.groups[l] = v.groups;
-                m.gexp[l] = v.gexp;
+                m.wmix[l] = v.wmix;
             }
         }
         if (G.nlev > 2)
@@ -1527,31 +1579,46 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
     // restriction, coarse levels and pass D: z into qf, <r, z> returned (valid in warp 0)
     auto finish_precondition = [&]() -> double {
         __syncthreads();
-        mg_restrict(m, 0, qf, B1, B2, 0);
+        if (m.n_groups[1] > 0) mg_restrict_runs(qf, B1, B2);
+        else mg_restrict(m, 0, qf, B1, B2, 0);
         __syncthreads();
         mg_coarse_cycle();
         const float *Z1 = m.Z[1];
+        const int32_t *__restrict__ pinfo = m.pinfo;
         const int cB1 = m.Bp1[1], cB2 = m.Bp2[1];
         DF a[1] = {{0.f, 0.f}};
         front_sweep(
             ng, nchunk, W, g_mg_need,
             [&](int g) {
                 // z0 = c0 r + P Z_1: the group's four points u2 .. u2+3 (u2 a multiple of 4)
-                // take their last-axis parents from three level-1 values of each (x, y) row
+                // take their last-axis parents from three level-1 values of each (x, y)
+                // row: one row, or two along each axis whose fine coordinate is odd
                 const int32_t gw = __ldg(grp + g);
                 const int off = (gw >> 4) << 2, mask = gw & 15;
-                int u0, u1, u2;
-                mg_coords(off, B1, B2, u0, u1, u2);
-                const int a0 = u0 >> 1, a1 = u1 >> 1, n0 = (u0 & 1) + 1, n1 = (u1 & 1) + 1;
-                float c_0 = 0.f, c_1 = 0.f, c_2 = 0.f;
-                for (int x = 0; x < n0; ++x)
-                    for (int y = 0; y < n1; ++y) {
-                        const float *row = Z1 + ((size_t)(a0 + x + kMgPadDev) * cB1 + (a1 + y + kMgPadDev)) * cB2 +
-                                           (u2 >> 1) + kMgPadDev;
-                        c_0 += row[0];
-                        c_1 += row[1];
-                        c_2 += row[2];
-                    }
+                const int32_t pinf = __ldg(pinfo + g);
+                const bool ox = pinf & 2, oy = pinf & 1;
+                const float *rb = Z1 + (pinf >> 2);
+                const int sx = cB1 * cB2;
+                float c_0 = rb[0], c_1 = rb[1], c_2 = rb[2];
+                const float y0 = rb[cB2], y1 = rb[cB2 + 1], y2 = rb[cB2 + 2];
+                const float x0 = rb[sx], x1 = rb[sx + 1], x2 = rb[sx + 2];
+                const float xy0 = rb[sx + cB2], xy1 = rb[sx + cB2 + 1], xy2 = rb[sx + cB2 + 2];
+                if (oy) {
+                    c_0 += y0;
+                    c_1 += y1;
+                    c_2 += y2;
+                }
+                if (ox) {
+                    c_0 += x0;
+                    c_1 += x1;
+                    c_2 += x2;
+                }
+                if (ox && oy) {
+                    c_0 += xy0;
+                    c_1 += xy1;
+                    c_2 += xy2;
+                }
+                const int n0 = ox ? 2 : 1, n1 = oy ? 2 : 1;
                 const float wxy = (n0 == 2 ? 0.5f : 1.f) * (n1 == 2 ? 0.5f : 1.f);
                 const float4 r = ld4(rf + off);
                 st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f,
@@ -1899,6 +1966,26 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
     }
 }
 
+// One orbital's box seen from one pair: the box coordinates of the pair's grid
+// offset m are MOD(b + m, N) with b = MOD(g_ij - lo, N) taken once per pair
+// (the same as MOD(MOD(g_ij + m, N) - lo, N) of Eq. l2g, without the second
+// wrap per point).
+struct PairBox {
+    int b[3];
+    __device__ PairBox(const CellDev &C, const int32_t *lo, int o, const int *g)
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) b[a] = wrapi(g[a] - lo[3 * o + a], C.n[a]);
+    }
+    // element index in a box of size dim, or -1 outside it
+    __device__ __forceinline__ long long at(const CellDev &C, const int *dim, int m0, int m1, int m2) const
+    {
+        const int u0 = wrapi(b[0] + m0, C.n[0]), u1 = wrapi(b[1] + m1, C.n[1]), u2 = wrapi(b[2] + m2, C.n[2]);
+        if (u0 >= dim[0] || u1 >= dim[1] || u2 >= dim[2]) return -1;
+        return ((long long)u0 * dim[1] + u1) * dim[2] + u2;
+    }
+};
+
 // |b|^2 for b = 4 pi rho + L v with v zero on PE and the far field on the halo
 // (v as double-float pairs), the stencil in FP32 and the sum in double-float.
 // Only the stopping threshold tol |b| uses it when the CG starts from the
@@ -1930,6 +2017,60 @@ __device__ __noinline__ double bnorm2_f32(const SetDev &S, const float2 *__restr
     if (threadIdx.x == 0) s_bn2 = (double)a[0].hi + (double)a[0].lo;
     __syncthreads();
     return s_bn2;
+}
+
+// D^i += v phi_j and D^j += v phi_i on the PE points and the shell (Eq. Dxx,
+// Step V), v on the shell from the multipole expansion (Eq. me): FP32 Cartesian
+// recurrences on the mixed path, the FP64 table otherwise.  Returns false when
+// a non-zero value falls outside a D box.
+__device__ __noinline__ bool d_scatter(const SetDev &S, const SmemCell &sm, const PairRec &pr,
+                                       const double *__restrict__ vbox, bool self, bool mixed)
+{
+    const CellDev &C = sm.C;
+    const PairBox fi(C, C.box_lo, pr.i, pr.g), fj(C, C.box_lo, pr.j, pr.g);
+    const PairBox di(C, C.dbox_lo, pr.i, pr.g), dj(C, C.dbox_lo, pr.j, pr.g);
+    const size_t bvol = (size_t)C.box[0] * C.box[1] * C.box[2], dvol = (size_t)C.dbox[0] * C.dbox[1] * C.dbox[2];
+    const double *__restrict__ phi_i = C.phi + (size_t)pr.i * bvol;
+    const double *__restrict__ phi_j = C.phi + (size_t)pr.j * bvol;
+    double *dx_i = C.dxx + (size_t)pr.i * dvol;
+    double *dx_j = C.dxx + (size_t)pr.j * dvol;
+    bool ok = true;
+    for (int k = threadIdx.x; k < S.n_pe + S.n_shell; k += blockDim.x) {
+        int m0, m1, m2;
+        double v;
+        if (k < S.n_pe) {
+            unpack_m(__ldg(S.pe_m + k), m0, m1, m2);
+            v = vbox[__ldg(S.pe_off + k)];
+        } else {
+            const int s = k - S.n_pe;
+            const int32_t pm = __ldg(S.sh_m + s);
+            unpack_m(pm, m0, m1, m2);
+            if (mixed) {
+                float x, y, z;
+                xyz_of(sm.hf, pm, x, y, z);
+                const RinvPows rp(rsqrtf(x * x + y * y + z * z));
+                v = solid_sum32(x, y, z, C.lmax, sm.cn, [&](int i, int l) { return rp.f[l] * sm.Qc[i]; });
+            } else {
+                v = 0.0;
+                for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * __ldg(S.T64 + (size_t)lm * S.n_shell + s);
+            }
+        }
+        {
+            const long long a = fj.at(C, C.box, m0, m1, m2);
+            const double val = v * (a >= 0 ? __ldg(phi_j + a) : 0.0);
+            const long long d = di.at(C, C.dbox, m0, m1, m2);
+            if (d >= 0) atomicAdd(dx_i + d, val);
+            else ok &= val == 0.0;
+        }
+        if (!self) {
+            const long long a = fi.at(C, C.box, m0, m1, m2);
+            const double val = v * (a >= 0 ? __ldg(phi_i + a) : 0.0);
+            const long long d = dj.at(C, C.dbox, m0, m1, m2);
+            if (d >= 0) atomicAdd(dx_j + d, val);
+            else ok &= val == 0.0;
+        }
+    }
+    return ok;
 }
 
 template <class T>
@@ -2024,14 +2165,19 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         };
 
         // ---- Step III: pair density on PE, g = MOD(g_ij + m, N) (Eq. l2g) ----
-        for (int k = tid; k < S.n_pe; k += nt) {
-            int m0, m1, m2;
-            unpack_m(S.pe_m[k], m0, m1, m2);
-            const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
-                      g2 = wrapi(pr.g[2] + m2, C.n[2]);
-            const double rk = phi_at(C, pr.i, g0, g1, g2) * phi_at(C, pr.j, g0, g1, g2);
-            rho[k] = rk;
-            if (dfm) b2[k] = dw_split(kFourPi * rk);
+        {
+            const PairBox fi(C, C.box_lo, pr.i, pr.g), fj(C, C.box_lo, pr.j, pr.g);
+            const size_t bvol = (size_t)C.box[0] * C.box[1] * C.box[2];
+            const double *__restrict__ phi_i = C.phi + (size_t)pr.i * bvol;
+            const double *__restrict__ phi_j = C.phi + (size_t)pr.j * bvol;
+            for (int k = tid; k < S.n_pe; k += nt) {
+                int m0, m1, m2;
+                unpack_m(__ldg(S.pe_m + k), m0, m1, m2);
+                const long long a = fi.at(C, C.box, m0, m1, m2), b = fj.at(C, C.box, m0, m1, m2);
+                const double rk = (a >= 0 ? __ldg(phi_i + a) : 0.0) * (b >= 0 ? __ldg(phi_j + b) : 0.0);
+                rho[k] = rk;
+                if (dfm) b2[k] = dw_split(kFourPi * rk);
+            }
         }
         __syncthreads();
 
@@ -2320,37 +2466,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
 
         // ---- D^i += v phi_j, D^j += v phi_i on PE and shell (Eq. Dxx, Step V) ----
         if (C.dxx) {
-            bool ok = true;
-            for (int k = tid; k < S.n_pe + S.n_shell; k += nt) {
-                int m0, m1, m2;
-                double v;
-                if (k < S.n_pe) {
-                    unpack_m(S.pe_m[k], m0, m1, m2);
-                    v = vbox[S.pe_off[k]];
-                } else {
-                    const int s = k - S.n_pe;
-                    unpack_m(S.sh_m[s], m0, m1, m2);
-                    if (mixed) {
-                        // Eq. me evaluated in FP32 from the Cartesian recurrences
-                        float x, y, z;
-                        xyz_of(sm.hf, S.sh_m[s], x, y, z);
-                        const RinvPows rp(rsqrtf(x * x + y * y + z * z));
-                        v = solid_sum32(x, y, z, C.lmax, sm.cn, [&](int i, int l) { return rp.f[l] * sm.Qc[i]; });
-                    } else {
-                        v = 0.0;
-                        for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * S.T64[(size_t)lm * S.n_shell + s];
-                    }
-                }
-                const int g0 = wrapi(pr.g[0] + m0, C.n[0]), g1 = wrapi(pr.g[1] + m1, C.n[1]),
-                          g2 = wrapi(pr.g[2] + m2, C.n[2]);
-                const double fj = phi_at(C, pr.j, g0, g1, g2);
-                ok &= d_add(C, pr.i, g0, g1, g2, v * fj);
-                if (!self) {
-                    const double fi = phi_at(C, pr.i, g0, g1, g2);
-                    ok &= d_add(C, pr.j, g0, g1, g2, v * fi);
-                }
-            }
-            if (!ok) s_flag = 1;
+            if (!d_scatter(S, sm, pr, vbox, self, mixed)) s_flag = 1;
         }
 
         // ---- restore the all-zero boxes for the next pair ----

@@ -7,11 +7,14 @@
 namespace exx {
 
 constexpr int kRowThreads = 128;     // pair-list CTA size
+// two 512-thread CTAs per SM, each on its own pair: one CTA's barriers and
+// per-pair passes overlap the other's streaming passes (64 registers a thread
+// either way)
 #ifndef EXX_SOLVE_THREADS
-#define EXX_SOLVE_THREADS 1024
+#define EXX_SOLVE_THREADS 512
 #endif
 #ifndef EXX_SOLVE_MIN_BLOCKS
-#define EXX_SOLVE_MIN_BLOCKS 1
+#define EXX_SOLVE_MIN_BLOCKS 2
 #endif
 constexpr int kSolveThreads = EXX_SOLVE_THREADS;       // persistent pair-solver CTA size
 constexpr int kSolveMinBlocks = EXX_SOLVE_MIN_BLOCKS;  // resident CTAs per SM it is compiled for

@@ -927,6 +927,31 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
         r.n_pure[l] = (int)r.groups[l].size();
         r.groups[l].insert(r.groups[l].end(), mixed_g.begin(), mixed_g.end());
         r.gexp[l].insert(r.gexp[l].end(), mixed_e.begin(), mixed_e.end());
+        const size_t nm = mixed_g.size();
+        r.wmix[l].assign(125 * nm * 4, 0.f);
+        for (size_t g = 0; g < nm; ++g)
+            for (int pos = 0; pos < 125; ++pos) {
+                const int k = r.kmap[l][pos];
+                if (k < 0) continue;
+                for (int i = 0; i < 4; ++i) {
+                    if (!(mixed_g[g] & (1 << i))) continue;
+                    const int e = mixed_e[4 * g + i];
+                    r.wmix[l][((size_t)pos * nm + g) * 4 + i] =
+                        e < 0 ? r.wdense[l][pos] : r.wexp[l][(size_t)k * n_exp + e];
+                }
+            }
+    }
+    // prolongation of level 1 onto the fine groups
+    if (nl >= 2) {
+        r.pinfo.resize(L.groups.size());
+        for (size_t g = 0; g < L.groups.size(); ++g) {
+            int u[3];
+            coords(L.B, (long long)(L.groups[g] >> 4) << 2, u);
+            const long long base = (((long long)(u[0] >> 1) + kMgPad) * r.Bp[1][1] + (u[1] >> 1) + kMgPad) * r.Bp[1][2] +
+                                   (u[2] >> 1) + kMgPad;
+            if (base >= (1LL << 29)) return EXX_ERR_ARG;
+            r.pinfo[g] = (int32_t)(base << 2 | (u[0] & 1) << 1 | (u[1] & 1));
+        }
     }
     t = std::move(r);
     return EXX_OK;

@@ -140,9 +140,18 @@ struct MgTables {
     // interior or inactive); runs without explicit rows first
     std::vector<int32_t> groups[kMgMaxLevels], gexp[kMgMaxLevels];   // gexp: [n_groups][4]
     int n_pure[kMgMaxLevels] = {};                  // leading runs whose points are all interior
+    // weights of the other runs by window position, four points at a time:
+    // [125][n_groups - n_pure][4], the interior weight for interior points, the
+    // point's own row for the others, zero for inactive points and outside the pattern
+    std::vector<float> wmix[kMgMaxLevels];
     float wdense[kMgMaxLevels][125] = {};           // interior stencil on the 5 x 5 x 5 window (dx, dy, dz)
     int kmap[kMgMaxLevels][125] = {};               // window position -> pattern entry k, -1 outside the pattern
     std::vector<float> cinv;                        // [n][n] of the coarsest level
+    // per aligned fine group (SetLayout::groups): the level-1 box offset of the
+    // last-axis parents of its first point in the row (u0/2, u1/2), shifted left
+    // by 2, with u0 & 1 in bit 1 and u1 & 1 in bit 0 (odd rows also read the
+    // next level-1 row along that axis)
+    std::vector<int32_t> pinfo;
     long long slot_floats = 0;                      // three boxes per coarse level
 };
 int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t);

@@ -354,7 +354,8 @@ int main(int argc, char **argv)
     MgTables T;
     if (make_mg_tables(L, st, 3, 200, 0.8, T)) return 5;
     int k2 = -1, n_exp1 = 0;
-    double rel2 = 1.0;
+    double rel2 = 1.0, runs_rel = 1.0, rruns_rel = 1.0, pinfo_rel = 1.0;
+    bool aligned = true;
     if (T.nlev >= 2) {
         std::vector<MgLevel> lv2;
         make_mg_levels(L, st, 3, 200, lv2);
@@ -370,6 +371,113 @@ int main(int argc, char **argv)
         }
         rel2 = std::sqrt(d2 / n2);
         n_exp1 = T.n_exp[1];
+        // level 1 in the solver's run form: runs of 4 points, interior runs from the
+        // dense window, the others from wmix, against the row form of apply()
+        {
+            std::vector<float> x(T.box[1], 0.f), y, yr(T.box[1], 0.f);
+            unsigned st_ = 12345u;
+            for (int i = 0; i < T.n[1]; ++i) {
+                st_ = st_ * 1664525u + 1013904223u;
+                x[T.pts[1][i]] = (float)((st_ >> 8) * (1.0 / 16777216.0) - 0.5);
+            }
+            mt.apply(1, x, y);
+            const int B1 = T.Bp[1][1], B2 = T.Bp[1][2];
+            const int ngr = (int)T.groups[1].size(), npure = T.n_pure[1], nm = ngr - npure;
+            for (int g = 0; g < ngr; ++g) {
+                const int off = (T.groups[1][g] >> 4) << 2, mask = T.groups[1][g] & 15;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int dxy = 0; dxy < 25; ++dxy)
+                    for (int dz = 0; dz < 5; ++dz) {
+                        const int pos = dxy * 5 + dz;
+                        if (T.kmap[1][pos] < 0) continue;
+                        const long long row = off + (long long)((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
+                        for (int i = 0; i < 4; ++i) {
+                            const float w = g < npure ? T.wdense[1][pos]
+                                                      : T.wmix[1][((size_t)pos * nm + (g - npure)) * 4 + i];
+                            acc[i] += w * x[row + i + dz - 2];
+                        }
+                    }
+                for (int i = 0; i < 4; ++i)
+                    if (mask & (1 << i)) yr[off + i] = acc[i];
+            }
+            double dd = 0.0, nn = 0.0;
+            for (int i = 0; i < T.n[1]; ++i) {
+                const long long o = T.pts[1][i];
+                dd = std::fmax(dd, std::fabs((double)yr[o] - (double)y[o]));
+                nn = std::fmax(nn, std::fabs((double)y[o]));
+            }
+            runs_rel = dd / nn;
+            // fine -> level 1 restriction by runs: three aligned groups of four fine values per row
+            const size_t fbox = (size_t)lv2[0].B[0] * lv2[0].B[1] * lv2[0].B[2];
+            std::vector<float> fb(fbox, 0.f), cb, cr(T.box[1], 0.f);
+            for (int i = 0; i < lv2[0].n; ++i) {
+                st_ = st_ * 1664525u + 1013904223u;
+                fb[lv2[0].pts[i]] = (float)((st_ >> 8) * (1.0 / 16777216.0) - 0.5);
+            }
+            mt.restrict_to(0, fb, cb);
+            const int F1 = lv2[0].B[1], F2 = lv2[0].B[2];
+            for (int g = 0; g < ngr; ++g) {
+                const int off = (T.groups[1][g] >> 4) << 2, mask = T.groups[1][g] & 15;
+                int c[3];
+                mt.coords(1, off, c);
+                if ((2 * c[2]) % 4 != 0) aligned = false;
+                for (int i = 0; i < 4; ++i) {
+                    if (!(mask & (1 << i))) continue;
+                    float s = 0.f;
+                    for (int dx = -1; dx <= 1; ++dx)
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            const long long row = ((long long)(2 * c[0] + dx) * F1 + (2 * c[1] + dy)) * F2 + 2 * c[2];
+                            const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f);
+                            s += w * (fb[row + 2 * i] + 0.5f * (fb[row + 2 * i - 1] + fb[row + 2 * i + 1]));
+                        }
+                    cr[off + i] = s;
+                }
+            }
+            dd = nn = 0.0;
+            for (int i = 0; i < T.n[1]; ++i) {
+                const long long o = T.pts[1][i];
+                dd = std::fmax(dd, std::fabs((double)cr[o] - (double)cb[o]));
+                nn = std::fmax(nn, std::fabs((double)cb[o]));
+            }
+            rruns_rel = dd / nn;
+            // pass D's prolongation of level 1 onto the fine groups from pinfo,
+            // against the generic trilinear prolongation
+            std::vector<float> zc(T.box[1], 0.f);
+            for (int i = 0; i < T.n[1]; ++i) {
+                st_ = st_ * 1664525u + 1013904223u;
+                zc[T.pts[1][i]] = (float)((st_ >> 8) * (1.0 / 16777216.0) - 0.5);
+            }
+            if (T.pinfo.size() != L.groups.size()) pinfo_rel = 1.0;
+            else {
+                dd = nn = 0.0;
+                const long long sx = (long long)T.Bp[1][1] * T.Bp[1][2], sy = T.Bp[1][2];
+                for (size_t g = 0; g < L.groups.size(); ++g) {
+                    const long long off = (long long)(L.groups[g] >> 4) << 2;
+                    const int mask = L.groups[g] & 15;
+                    const int pi = T.pinfo[g];
+                    const bool ox = pi & 2, oy = pi & 1;
+                    const long long b = pi >> 2;
+                    float c[3];
+                    for (int k = 0; k < 3; ++k) {
+                        c[k] = zc[b + k];
+                        if (oy) c[k] += zc[b + sy + k];
+                        if (ox) c[k] += zc[b + sx + k];
+                        if (ox && oy) c[k] += zc[b + sx + sy + k];
+                    }
+                    const float wxy = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+                    const float zv[4] = {wxy * c[0], wxy * 0.5f * (c[0] + c[1]), wxy * c[1], wxy * 0.5f * (c[1] + c[2])};
+                    for (int i = 0; i < 4; ++i) {
+                        if (!(mask & (1 << i))) continue;
+                        int u[3];
+                        mt.coords(0, off + i, u);
+                        const double ref = mt.prolong_at(0, zc, u);
+                        dd = std::fmax(dd, std::fabs((double)zv[i] - ref));
+                        nn = std::fmax(nn, std::fabs(ref));
+                    }
+                }
+                pinfo_rel = dd / nn;
+            }
+        }
     }
     double d = 0.0, nx = 0.0;
     for (int i = 0; i < A.n; ++i) {
@@ -382,7 +490,10 @@ int main(int argc, char **argv)
     for (size_t l = 0; l < mg.lv.size(); ++l) std::printf("%s%d", l ? ", " : "", mg.lv[l].n);
     std::printf("], \"n_stcl\": %d, \"cg_iter\": %d, \"pcg_iter\": %d, \"rel_diff\": %.3e, \"asym\": %.3e, "
                 "\"level1_max_nnz\": %d, \"tables_levels\": %d, \"tables_pcg_iter\": %d, "
-                "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d}\n",
-                2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1]);
+                "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d, "
+                "\"runs_rel_diff\": %.3e, \"restrict_runs_rel_diff\": %.3e, \"restrict_runs_aligned\": %d, "
+                "\"prolong_groups_rel_diff\": %.3e}\n",
+                2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1],
+                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel);
     return 0;
 }

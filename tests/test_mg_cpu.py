@@ -47,3 +47,10 @@ def test_vcycle_preconditioned_cg(harness, cell, n_stcl):
     assert 0 < r["tables_pcg_iter"] <= 20
     assert r["tables_rel_diff"] < 1e-8
     assert 0 < r["tables_level1_explicit"] < r["tables_level1_n"]
+    # the run forms the solver uses on level 1 (float4 weights per window position for
+    # runs with explicit rows; the fine restriction from aligned groups of four) give
+    # the row forms up to FP32 summation order
+    assert r["runs_rel_diff"] < 1e-5
+    assert r["restrict_runs_rel_diff"] < 1e-5 and r["restrict_runs_aligned"] == 1
+    # pass D's prolongation onto the fine groups (level-1 rows from the per-group table)
+    assert r["prolong_groups_rel_diff"] < 1e-6
