@@ -550,9 +550,10 @@ struct SmemCell {
     float cw32[6][8];
     float2 cwdf[6][8];   // cw64 as double-float pairs
     float2 centerdf;
-    float cn[kNlm];      // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0): solid_sum32
+    float cn[kNlm];      // N_l0 at l^2 + l, sqrt2 N_lm at l^2 + l + m (m > 0)
     float hf[3][3];      // h[a][b] / N_b: Cartesian position of a grid offset, FP32
     float Qc[kNlm];      // 4 pi / (2l+1) Q_lm of the current pair, FP32
+    float2 cq2[kNlm];    // at l^2 + l + m (m >= 0): cn Qc of (l, m) and of (l, -m), for solid_parts32
     float2 w1df[3][8];   // first-derivative weights w1dx as double-float pairs
     double Q[kNlm];
     float Qf[kNlm];
@@ -1220,32 +1221,45 @@ __shared__ MgSm g_mg_sm;          // one copy per kernel that uses the multigrid
 
 // Part of (A_l x) at active point i (box offset o) of coarse level l: the
 // pattern entries k = sub, sub + tpr, ... (tpr threads share a row on the small
-// levels).  Two independent partial sums keep several loads in flight.
+// levels).  U independent partial sums keep U weight and U value loads in
+// flight (explicit rows read their weights from L2, pattern-major).
+template <int U, class Wt>
+__device__ __forceinline__ float mg_row_sum(int K, const int *koff, const float *__restrict__ x, int o, int sub, int tpr,
+                                            Wt wt)
+{
+    float s[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) s[j] = 0.f;
+    int k = sub;
+    for (; k + (U - 1) * tpr < K; k += U * tpr) {
+        float wv[U], xv[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            wv[j] = wt(k + j * tpr);
+            xv[j] = x[o + koff[k + j * tpr]];
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) s[j] += wv[j] * xv[j];
+    }
+    for (; k < K; k += tpr) s[0] += wt(k) * x[o + koff[k]];
+    float t = s[0];
+#pragma unroll
+    for (int j = 1; j < U; ++j) t += s[j];
+    return t;
+}
 __device__ __forceinline__ float mg_row(int l, int i, int o, const float *__restrict__ x, int sub, int tpr)
 {
     const MgSm &m = g_mg_sm;
     const int K = m.K[l];
     const int *koff = m.koff[l];
-    float s0 = 0.f, s1 = 0.f;
     const int e = i - m.n_int[l];
-    int k = sub;
     if (e < 0) {
         const float *w = m.wint[l];
-        for (; k + tpr < K; k += 2 * tpr) {
-            s0 += w[k] * x[o + koff[k]];
-            s1 += w[k + tpr] * x[o + koff[k + tpr]];
-        }
-        if (k < K) s0 += w[k] * x[o + koff[k]];
-    } else {
-        const int ne = m.n_exp[l];
-        const float *__restrict__ w = m.wexp[l] + e;
-        for (; k + tpr < K; k += 2 * tpr) {
-            s0 += __ldg(w + (size_t)k * ne) * x[o + koff[k]];
-            s1 += __ldg(w + (size_t)(k + tpr) * ne) * x[o + koff[k + tpr]];
-        }
-        if (k < K) s0 += __ldg(w + (size_t)k * ne) * x[o + koff[k]];
+        return mg_row_sum<4>(K, koff, x, o, sub, tpr, [&](int k) { return w[k]; });
     }
-    return s0 + s1;
+    const int ne = m.n_exp[l];
+    const float *__restrict__ w = m.wexp[l] + e;
+    return mg_row_sum<6>(K, koff, x, o, sub, tpr, [&](int k) { return __ldg(w + (size_t)k * ne); });
 }
 
 // T = R - A_l X on coarse level 1, by runs of 4 points along the last axis:
@@ -1265,7 +1279,7 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
         const int off = (gw >> 4) << 2, mask = gw & 15;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         if (g < npure) {
-#pragma unroll 1
+#pragma unroll 5
             for (int dxy = 0; dxy < 25; ++dxy) {
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
                 const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
@@ -1282,7 +1296,7 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
             // one float4 of weights per window position for the run's four points
             const int nm = ng - npure;
             const float4 *__restrict__ wm = m.wmix[l] + (g - npure);
-#pragma unroll 1
+#pragma unroll 5
             for (int dxy = 0; dxy < 25; ++dxy) {
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
                 const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
@@ -1464,6 +1478,150 @@ struct MgScalars {
 };
 __shared__ MgScalars g_mg_cs;
 
+// The fine-level passes of the multigrid PCG, each an out-of-line function so
+// that its group loop has the registers to itself (the caller's state stays in
+// the caller's frame across the call).  Each returns its thread's part of the
+// pass's dot product as a double-float pair (hi, lo).
+
+// t = r + c0 L r on one group (the stencil half of pass B and the frame's first
+// pre-smoothing), into qf
+template <int FDN>
+__device__ __forceinline__ void mg_pre_smooth_group(const SetDev &S, const SmemCell &sm, const float *__restrict__ rf,
+                                                    float *__restrict__ qf, float c0, int g)
+{
+    const int32_t gw = __ldg(S.groups + g);
+    const int off = (gw >> 4) << 2, mask = gw & 15;
+    float acc[4];
+    lap4<FDN>(rf, off, sm.cw32, sm.center32, S.rstride, S.d2, sm.C.ndir, acc);
+    const float4 r = ld4(rf + off);
+    st4(qf + off, (mask & 1) ? r.x + c0 * acc[0] : 0.f, (mask & 2) ? r.y + c0 * acc[1] : 0.f,
+        (mask & 4) ? r.z + c0 * acc[2] : 0.f, (mask & 8) ? r.w + c0 * acc[3] : 0.f);
+}
+
+template <int FDN>
+__device__ __noinline__ void mg_pre_smooth_all(const SetDev &S, const SmemCell &sm, const float *rf, float *qf, float c0)
+{
+    for (int g = threadIdx.x; g < S.n_groups; g += blockDim.x) mg_pre_smooth_group<FDN>(S, sm, rf, qf, c0, g);
+}
+
+// pass A: p = z + beta p (p = z in a frame's first iteration; z is in qf) ahead
+// of q = A p into qf, <p, q>
+template <int FDN>
+__device__ __noinline__ float2 mg_pass_a(const SetDev &S, const SmemCell &sm, float *__restrict__ pf,
+                                         float *__restrict__ qf, float beta, bool copy, int nchunk, int W)
+{
+    const int32_t *__restrict__ grp = S.groups;
+    DF a = {0.f, 0.f};
+    front_sweep(
+        S.n_groups, nchunk, W, g_mg_need,
+        [&](int g) {
+            const int off = (__ldg(grp + g) >> 4) << 2;
+            const float4 z = ld4(qf + off);
+            if (copy) {
+                *reinterpret_cast<float4 *>(pf + off) = z;
+            } else {
+                const float4 p = ld4(pf + off);
+                st4(pf + off, z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w);
+            }
+        },
+        [&](int g) {
+            const int32_t gw = __ldg(grp + g);
+            const int off = (gw >> 4) << 2, mask = gw & 15;
+            float acc[4];
+            const float4 p = lap4<FDN>(pf, off, sm.cw32, sm.center32, S.rstride, S.d2, sm.C.ndir, acc);
+            const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
+            const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
+            st4(qf + off, q0, q1, q2, q3);
+            df_add(a, p.x * q0 + p.y * q1 + p.z * q2 + p.w * q3);
+        });
+    return make_float2(a.hi, a.lo);
+}
+
+// pass B: r -= alpha q, e += alpha p (<r, r>) ahead of t = r + c0 L r into qf
+template <int FDN>
+__device__ __noinline__ float2 mg_pass_b(const SetDev &S, const SmemCell &sm, float *__restrict__ rf,
+                                         float *__restrict__ qf, const float *__restrict__ pf, float *__restrict__ ef,
+                                         float alpha, float c0, int nchunk, int W)
+{
+    const int32_t *__restrict__ grp = S.groups;
+    DF b = {0.f, 0.f};
+    front_sweep(
+        S.n_groups, nchunk, W, g_mg_need,
+        [&](int g) {
+            const int off = (__ldg(grp + g) >> 4) << 2;
+            const float4 r = ld4(rf + off), q = ld4(qf + off), p = ld4(pf + off), e = ld4(ef + off);
+            const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z, r3 = r.w - alpha * q.w;
+            st4(rf + off, r0, r1, r2, r3);
+            st4(ef + off, e.x + alpha * p.x, e.y + alpha * p.y, e.z + alpha * p.z, e.w + alpha * p.w);
+            df_add(b, r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+        },
+        [&](int g) { mg_pre_smooth_group<FDN>(S, sm, rf, qf, c0, g); });
+    return make_float2(b.hi, b.lo);
+}
+
+// pass D: z0 = c0 r + P Z_1 into zf ahead of z = z0 + c0 (r + L z0) into qf, <r, z>.
+// The group's four points u2 .. u2+3 (u2 a multiple of 4) take their last-axis
+// parents from three level-1 values of each (x, y) row: one row, or two along
+// each axis whose fine coordinate is odd (pinfo).
+template <int FDN>
+__device__ __noinline__ float2 mg_pass_d(const SetDev &S, const SmemCell &sm, const float *__restrict__ rf,
+                                         float *__restrict__ zf, float *__restrict__ qf, float c0, int nchunk, int W)
+{
+    const MgSm &m = g_mg_sm;
+    const int32_t *__restrict__ grp = S.groups;
+    const int32_t *__restrict__ pinfo = m.pinfo;
+    const float *__restrict__ Z1 = m.Z[1];
+    const int cB2 = m.Bp2[1], sx = m.Bp1[1] * m.Bp2[1];
+    DF a = {0.f, 0.f};
+    front_sweep(
+        S.n_groups, nchunk, W, g_mg_need,
+        [&](int g) {
+            const int32_t gw = __ldg(grp + g);
+            const int off = (gw >> 4) << 2, mask = gw & 15;
+            const int32_t pinf = __ldg(pinfo + g);
+            const bool ox = pinf & 2, oy = pinf & 1;
+            const float *rb = Z1 + (pinf >> 2);
+            float c_0 = rb[0], c_1 = rb[1], c_2 = rb[2];
+            const float y0 = rb[cB2], y1 = rb[cB2 + 1], y2 = rb[cB2 + 2];
+            const float x0 = rb[sx], x1 = rb[sx + 1], x2 = rb[sx + 2];
+            const float xy0 = rb[sx + cB2], xy1 = rb[sx + cB2 + 1], xy2 = rb[sx + cB2 + 2];
+            if (oy) {
+                c_0 += y0;
+                c_1 += y1;
+                c_2 += y2;
+            }
+            if (ox) {
+                c_0 += x0;
+                c_1 += x1;
+                c_2 += x2;
+            }
+            if (ox && oy) {
+                c_0 += xy0;
+                c_1 += xy1;
+                c_2 += xy2;
+            }
+            const float wxy = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+            const float4 r = ld4(rf + off);
+            st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f,
+                (mask & 2) ? c0 * r.y + wxy * 0.5f * (c_0 + c_1) : 0.f, (mask & 4) ? c0 * r.z + wxy * c_1 : 0.f,
+                (mask & 8) ? c0 * r.w + wxy * 0.5f * (c_1 + c_2) : 0.f);
+        },
+        [&](int g) {
+            const int32_t gw = __ldg(grp + g);
+            const int off = (gw >> 4) << 2, mask = gw & 15;
+            float acc[4];
+            const float4 z0 = lap4<FDN>(zf, off, sm.cw32, sm.center32, S.rstride, S.d2, sm.C.ndir, acc);
+            const float4 r = ld4(rf + off);
+            const float z_0 = (mask & 1) ? z0.x + c0 * (r.x + acc[0]) : 0.f;
+            const float z_1 = (mask & 2) ? z0.y + c0 * (r.y + acc[1]) : 0.f;
+            const float z_2 = (mask & 4) ? z0.z + c0 * (r.z + acc[2]) : 0.f;
+            const float z_3 = (mask & 8) ? z0.w + c0 * (r.w + acc[3]) : 0.f;
+            st4(qf + off, z_0, z_1, z_2, z_3);
+            df_add(a, r.x * z_0 + r.y * z_1 + r.z * z_2 + r.w * z_3);
+        });
+    return make_float2(a.hi, a.lo);
+}
+
 // The mixed-precision solve of one pair with the multigrid preconditioner (see
 // the comment above MgSm).  zf: one more dense FP32 box; mgbase: the slot's
 // region for the coarse boxes.  One PCG iteration is four passes over the fine
@@ -1489,9 +1647,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
     const int32_t *__restrict__ poff = S.pe_off;
     const int32_t *__restrict__ grp = S.groups;
     const int npe = S.n_pe, ng = S.n_groups, ndir = cg.ndir;
-    const int *rs = S.rstride, *dsf = S.dstride, *d2 = S.d2;
-    const float(*cw)[8] = sm.cw32;
-    const float center = sm.center32;
+    const int *rs = S.rstride, *dsf = S.dstride;
     const double stop = cg.stop, inner_red = cg.inner_red;
     float2 *red2 = reinterpret_cast<float2 *>(cg.red);
     const int B1 = S.B[1], B2 = S.B[2];
@@ -1566,16 +1722,6 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
     if (!(cg.r0n > stop)) return;   // the starting guess already meets the tolerance
     const float c0 = m.c0;
 
-    // the stencil half of pass B: t = r + c0 L r into qf
-    auto pre_smooth = [&](int g) {
-        const int32_t gw = __ldg(grp + g);
-        const int off = (gw >> 4) << 2, mask = gw & 15;
-        float acc[4];
-        lap_group<FDN>(rf, off, cw, center, rs, dsf, d2, ndir, acc);
-        const float4 r = ld4(rf + off);
-        st4(qf + off, (mask & 1) ? r.x + c0 * acc[0] : 0.f, (mask & 2) ? r.y + c0 * acc[1] : 0.f,
-            (mask & 4) ? r.z + c0 * acc[2] : 0.f, (mask & 8) ? r.w + c0 * acc[3] : 0.f);
-    };
     // restriction, coarse levels and pass D: z into qf, <r, z> returned (valid in warp 0)
     auto finish_precondition = [&]() -> double {
         __syncthreads();
@@ -1583,62 +1729,8 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
         else mg_restrict(m, 0, qf, B1, B2, 0);
         __syncthreads();
         mg_coarse_cycle();
-        const float *Z1 = m.Z[1];
-        const int32_t *__restrict__ pinfo = m.pinfo;
-        const int cB1 = m.Bp1[1], cB2 = m.Bp2[1];
-        DF a[1] = {{0.f, 0.f}};
-        front_sweep(
-            ng, nchunk, W, g_mg_need,
-            [&](int g) {
-                // z0 = c0 r + P Z_1: the group's four points u2 .. u2+3 (u2 a multiple of 4)
-                // take their last-axis parents from three level-1 values of each (x, y)
-                // row: one row, or two along each axis whose fine coordinate is odd
-                const int32_t gw = __ldg(grp + g);
-                const int off = (gw >> 4) << 2, mask = gw & 15;
-                const int32_t pinf = __ldg(pinfo + g);
-                const bool ox = pinf & 2, oy = pinf & 1;
-                const float *rb = Z1 + (pinf >> 2);
-                const int sx = cB1 * cB2;
-                float c_0 = rb[0], c_1 = rb[1], c_2 = rb[2];
-                const float y0 = rb[cB2], y1 = rb[cB2 + 1], y2 = rb[cB2 + 2];
-                const float x0 = rb[sx], x1 = rb[sx + 1], x2 = rb[sx + 2];
-                const float xy0 = rb[sx + cB2], xy1 = rb[sx + cB2 + 1], xy2 = rb[sx + cB2 + 2];
-                if (oy) {
-                    c_0 += y0;
-                    c_1 += y1;
-                    c_2 += y2;
-                }
-                if (ox) {
-                    c_0 += x0;
-                    c_1 += x1;
-                    c_2 += x2;
-                }
-                if (ox && oy) {
-                    c_0 += xy0;
-                    c_1 += xy1;
-                    c_2 += xy2;
-                }
-                const int n0 = ox ? 2 : 1, n1 = oy ? 2 : 1;
-                const float wxy = (n0 == 2 ? 0.5f : 1.f) * (n1 == 2 ? 0.5f : 1.f);
-                const float4 r = ld4(rf + off);
-                st4(zf + off, (mask & 1) ? c0 * r.x + wxy * c_0 : 0.f,
-                    (mask & 2) ? c0 * r.y + wxy * 0.5f * (c_0 + c_1) : 0.f, (mask & 4) ? c0 * r.z + wxy * c_1 : 0.f,
-                    (mask & 8) ? c0 * r.w + wxy * 0.5f * (c_1 + c_2) : 0.f);
-            },
-            [&](int g) {
-                // z = z0 + c0 (r - A z0) = z0 + c0 (r + L z0)
-                const int32_t gw = __ldg(grp + g);
-                const int off = (gw >> 4) << 2, mask = gw & 15;
-                float acc[4];
-                lap_group<FDN>(zf, off, cw, center, rs, dsf, d2, ndir, acc);
-                const float4 r = ld4(rf + off), z0 = ld4(zf + off);
-                const float z_0 = (mask & 1) ? z0.x + c0 * (r.x + acc[0]) : 0.f;
-                const float z_1 = (mask & 2) ? z0.y + c0 * (r.y + acc[1]) : 0.f;
-                const float z_2 = (mask & 4) ? z0.z + c0 * (r.z + acc[2]) : 0.f;
-                const float z_3 = (mask & 8) ? z0.w + c0 * (r.w + acc[3]) : 0.f;
-                st4(qf + off, z_0, z_1, z_2, z_3);
-                df_add(a[0], r.x * z_0 + r.y * z_1 + r.z * z_2 + r.w * z_3);
-            });
+        const float2 d = mg_pass_d<FDN>(S, sm, rf, zf, qf, c0, nchunk, W);
+        DF a[1] = {{d.x, d.y}};
         block_sum_df<1>(a, red2);
         return (double)a[0].hi + (double)a[0].lo;
     };
@@ -1661,7 +1753,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             __syncthreads();
         }
         // z = M r from the frame's residual (pass B without its update)
-        for (int g = tid; g < ng; g += nt) pre_smooth(g);
+        mg_pre_smooth_all<FDN>(S, sm, rf, qf, c0);
         const double rz0 = finish_precondition();
         if (tid == 0) {
             cs.rz = rz0;
@@ -1680,30 +1772,8 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             const float beta = cs.beta;
             const bool copy = first;
             first = false;
-            DF a[1] = {{0.f, 0.f}};
-            front_sweep(
-                ng, nchunk, W, g_mg_need,
-                [&](int g) {
-                    const int off = (__ldg(grp + g) >> 4) << 2;
-                    const float4 z = ld4(qf + off);
-                    if (copy) {
-                        *reinterpret_cast<float4 *>(pf + off) = z;
-                    } else {
-                        const float4 p = ld4(pf + off);
-                        st4(pf + off, z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w);
-                    }
-                },
-                [&](int g) {
-                    const int32_t gw = __ldg(grp + g);
-                    const int off = (gw >> 4) << 2, mask = gw & 15;
-                    float acc[4];
-                    lap_group<FDN>(pf, off, cw, center, rs, dsf, d2, ndir, acc);
-                    const float4 p = ld4(pf + off);
-                    const float q0 = (mask & 1) ? -acc[0] : 0.f, q1 = (mask & 2) ? -acc[1] : 0.f;
-                    const float q2 = (mask & 4) ? -acc[2] : 0.f, q3 = (mask & 8) ? -acc[3] : 0.f;
-                    st4(qf + off, q0, q1, q2, q3);
-                    df_add(a[0], p.x * q0 + p.y * q1 + p.z * q2 + p.w * q3);
-                });
+            const float2 pa = mg_pass_a<FDN>(S, sm, pf, qf, beta, copy, nchunk, W);
+            DF a[1] = {{pa.x, pa.y}};
             block_sum_df<1>(a, red2);
             if (tid == 0) {
                 const double pq = (double)a[0].hi + (double)a[0].lo;
@@ -1716,19 +1786,8 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             int act = cs.act;
             if (!act) {
                 // pass B: e += alpha p, r -= alpha q (<r, r>) ahead of t = r + c0 L r
-                DF b[1] = {{0.f, 0.f}};
-                front_sweep(
-                    ng, nchunk, W, g_mg_need,
-                    [&](int g) {
-                        const int off = (__ldg(grp + g) >> 4) << 2;
-                        const float4 r = ld4(rf + off), q = ld4(qf + off), p = ld4(pf + off), e = ld4(ef + off);
-                        const float r0 = r.x - alpha * q.x, r1 = r.y - alpha * q.y, r2 = r.z - alpha * q.z,
-                                    r3 = r.w - alpha * q.w;
-                        st4(rf + off, r0, r1, r2, r3);
-                        st4(ef + off, e.x + alpha * p.x, e.y + alpha * p.y, e.z + alpha * p.z, e.w + alpha * p.w);
-                        df_add(b[0], r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-                    },
-                    pre_smooth);
+                const float2 pb = mg_pass_b<FDN>(S, sm, rf, qf, pf, ef, alpha, c0, nchunk, W);
+                DF b[1] = {{pb.x, pb.y}};
                 block_sum_df<1>(b, red2);
                 if (tid == 0) {
                     const double rr = (double)b[0].hi + (double)b[0].lo;
@@ -1776,26 +1835,28 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
 // with |r'| < r decided by radial bin (half of the point's own bin on each side).
 // Outside PE this is the far field of Eq. me, which is why it is close to the
 // solution of Eq. pe; it only sets where CG starts, not what it converges to.
-// gs: scratch of the CTA, [2][2 kGuessBins][kNlm] moments per half bin, then
-// [2][kGuessBins][kNlm] cumulative inner and outer moments per bin.
+// gs: scratch of the CTA, [2][2 kGuessBins][kNlm] moments per half bin (later
+// overwritten by the guess's per-bin coefficients, [kGuessBins][kNlm] float4),
+// then [2][kGuessBins][kNlm] cumulative inner and outer moments per bin.
 constexpr double kWarmAccept = 0.05;   // warm starts kept when |b - A v_prev| <= 5 % of |b|
 
-__device__ __forceinline__ float rinv_pow(float ri, int l)   // ri^(2l+1), l <= 7, without branches
-{
-    const float r2 = ri * ri, r4 = r2 * r2, r8 = r4 * r4;
-    return ri * ((l & 1) ? r2 : 1.f) * ((l & 2) ? r4 : 1.f) * ((l & 4) ? r8 : 1.f);
-}
-
-// sum over lm (l <= lmax) of S_lm(x, y, z) coef(lm, l), with r^l Y_lm from the
-// Cartesian recurrences of solid_harmonics evaluated in FP32 (about 1e-6 of
-// the largest term, against 6e-8 for the rounded FP64 tables); cn holds N_l0
-// at l^2 + l and sqrt2 N_lm at l^2 + l + m.
-template <class Coef>
-__device__ __forceinline__ float solid_sum32(float x, float y, float z, int lmax, const float *cn, const Coef &coef)
+// Sums over lm (l <= lmax) of S_lm(x, y, z) times coefficients, with r^l Y_lm
+// from the Cartesian recurrences of solid_harmonics evaluated in FP32 (about
+// 1e-6 of the largest term, against 6e-8 for the rounded FP64 tables),
+// summed per degree: for NC coefficient channels,
+// vl[c][l] = sum_m Q_l^m (A_m cf_c(l, m) + B_m cf_c(l, -m)) (Q_l^0 cf_c(l, 0) for
+// m = 0), with the normalisation N_lm already folded into the coefficients.  cf
+// fills k[2c] = cf_c(l, m) and k[2c + 1] = cf_c(l, -m).  The caller weights
+// each degree (r^-(2l+1) for a far field), so no per-term factor of r is needed.
+template <int NC, class Cf>
+__device__ __forceinline__ void solid_parts32(float x, float y, float z, int lmax, const Cf &cf, float (&vl)[NC][7])
 {
     const float r2 = x * x + y * y + z * z;
-    float v = 0.f;
-    float Am = 1.f, Bm = 0.f, dfact = 1.f;   // (x + iy)^m, (2m-1)!!
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int l = 0; l < 7; ++l) vl[c][l] = 0.f;
+    float Am = 1.f, Bm = 0.f, dfact = 1.f;
 #pragma unroll
     for (int m = 0; m <= 6; ++m) {
         if (m > 0) {
@@ -1804,7 +1865,7 @@ __device__ __forceinline__ float solid_sum32(float x, float y, float z, int lmax
             Am = An;
             dfact *= (float)(2 * m - 1);
         }
-        float q1 = 0.f, q2 = 0.f;   // Q_{l-1}^m, Q_{l-2}^m
+        float q1 = 0.f, q2 = 0.f;
 #pragma unroll
         for (int l = m; l <= 6; ++l) {
             float q;
@@ -1814,14 +1875,16 @@ __device__ __forceinline__ float solid_sum32(float x, float y, float z, int lmax
             q2 = q1;
             q1 = q;
             if (l <= lmax) {
-                const int i0 = l * l + l;
-                const float c = cn[i0 + m] * q;
-                if (m == 0) v += c * coef(i0, l);
-                else v += c * (Am * coef(i0 + m, l) + Bm * coef(i0 - m, l));
+                float k[2 * NC];
+                cf(l, m, k);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (m == 0) vl[c][l] += q * k[2 * c];
+                    else vl[c][l] += q * (Am * k[2 * c] + Bm * k[2 * c + 1]);
+                }
             }
         }
     }
-    return v;
 }
 
 // r^-(2l+1), l = 0..6, from 1/r
@@ -1863,7 +1926,8 @@ __device__ __forceinline__ void pe_xyz(const SetDev &S, const float (*h)[3], int
 // moments rho r^-(l+1) Y_lm dV (FP32), and qpart[w] the FP64 sum of the inner
 // moments of warp w's pieces; their sum over the warps is the moment Q_lm of
 // Eq. mepole (up to dV), accumulated like the one-pass moments: FP32 over 32
-// points, FP64 beyond.
+// points, FP64 beyond.  Per 32 points the warp stages rho and rho r^-(2l+1)
+// (l = 0..6) in shared memory, so each table row costs two loads and four FMAs.
 constexpr int kGuessPieces = 2 * kGuessBins;
 __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, const double *__restrict__ rho,
                                          float *__restrict__ gs, double (*qpart)[kNlm])
@@ -1878,6 +1942,8 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
         for (int b = 0; b < 3; ++b) h[a][b] = (float)(C.h[a][b] / C.n[b]);
     float *PA = gs, *PB = gs + kGuessPieces * kNlm;   // per piece j: bin kGuessBins - 1 - j / 2, half j % 2
     const double dv = C.dv;
+    __shared__ float s_mw[kSolveThreads / 32][32][8];
+    float(*mw)[8] = s_mw[warp];
     double w0 = 0.0, w1 = 0.0;
     for (int base = 0; base < kGuessPieces; base += nwarps) {   // each round a permutation of base + [0, nwarps)
         const int j = base + (((base / nwarps) & 1) ? nwarps - 1 - warp : warp);
@@ -1896,17 +1962,29 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
             const float r2 = px * px + py * py + pz * pz;
             const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
             const int xq = min(32, k1 - x);
+            // each lane's point: rho r^-(2l+1) for l = 0..6, and rho, for the warp to read
+            __syncwarp();
+            {
+                const float ri2 = ri * ri;
+                float pw = ri;
+#pragma unroll
+                for (int l = 0; l < 7; ++l) {
+                    mw[lane][l] = rl * pw;
+                    pw *= ri2;
+                }
+                mw[lane][7] = rl;
+            }
+            __syncwarp();
             float f0 = 0.f, f1 = 0.f;
 #pragma unroll 8
             for (int q = 0; q < 32; ++q) {
-                const float rp = __shfl_sync(0xffffffffu, rl, q);
-                const float rip = __shfl_sync(0xffffffffu, ri, q);
+                const float rp = mw[q][7];
                 const float *row = S.gs_S32 + (size_t)(x + min(q, xq - 1)) * kNlm;   // rows in sorted order
                 const float s0 = row[lane], s1 = row[lane1];
                 f0 += rp * s0;
                 f1 += rp * s1;
-                b0 += rp * s0 * rinv_pow(rip, l0);
-                b1 += rp * s1 * rinv_pow(rip, l1);
+                b0 += s0 * mw[q][l0];
+                b1 += s1 * mw[q][l1];
             }
             a0 += f0;
             a1 += f1;
@@ -1950,17 +2028,41 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
         }
     }
     __syncthreads();
+    // per bin and (l, m >= 0), over the per-piece moments (no longer needed):
+    // 4 pi / (2l+1) N_lm times the inner and outer sums of (l, m) and (l, -m)
+    float4 *G = reinterpret_cast<float4 *>(gs);
+    for (int t = tid; t < kGuessBins * kNlm; t += nt) {
+        const int b = t / kNlm, i = t - b * kNlm;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= i) ++l;
+        const int i0 = l * l + l, mm = i - i0;
+        const float K = (12.566370614359172f / (float)(2 * l + 1)) * cn[i];
+        const float *Ab = A + b * kNlm, *Bb = B + b * kNlm;
+        G[t] = mm < 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                      : make_float4(K * Ab[i], mm > 0 ? K * Ab[i0 - mm] : 0.f, K * Bb[i], mm > 0 ? K * Bb[i0 - mm] : 0.f);
+    }
+    __syncthreads();
     const int lmax = C.lmax;
     for (int j = tid; j < S.n_pe; j += nt) {
         const int kk = S.gs_perm[j];
-        const float *Ab = A + (int)S.gs_bin[kk] * kNlm, *Bb = B + (int)S.gs_bin[kk] * kNlm;
+        const float4 *Gb = G + (int)S.gs_bin[kk] * kNlm;
         float x, y, z;
         xyz_of(hf, S.pe_m[kk], x, y, z);
         const float r2 = x * x + y * y + z * z;
         const RinvPows rp(r2 > 0.f ? rsqrtf(r2) : 0.f);
-        const float v = solid_sum32(x, y, z, lmax, cn, [&](int i, int l) {
-            return (12.566370614359172f / (float)(2 * l + 1)) * (rp.f[l] * Ab[i] + Bb[i]);
-        });
+        float vl[2][7];
+        solid_parts32<2>(x, y, z, lmax,
+                         [&](int l, int m, float *k) {
+                             const float4 g = Gb[l * l + l + m];
+                             k[0] = g.x;
+                             k[1] = g.y;
+                             k[2] = g.z;
+                             k[3] = g.w;
+                         },
+                         vl);
+        float v = 0.f;
+#pragma unroll
+        for (int l = 0; l < 7; ++l) v += rp.f[l] * vl[0][l] + vl[1][l];
         if (df) reinterpret_cast<float2 *>(vbox)[S.pe_off[kk]] = make_float2(v, 0.f);   // double-float pair
         else vbox[S.pe_off[kk]] = (double)v;
     }
@@ -2049,7 +2151,18 @@ __device__ __noinline__ bool d_scatter(const SetDev &S, const SmemCell &sm, cons
                 float x, y, z;
                 xyz_of(sm.hf, pm, x, y, z);
                 const RinvPows rp(rsqrtf(x * x + y * y + z * z));
-                v = solid_sum32(x, y, z, C.lmax, sm.cn, [&](int i, int l) { return rp.f[l] * sm.Qc[i]; });
+                float vl[1][7];
+                solid_parts32<1>(x, y, z, C.lmax,
+                                 [&](int l, int m, float *k) {
+                                     const float2 c = sm.cq2[l * l + l + m];
+                                     k[0] = c.x;
+                                     k[1] = c.y;
+                                 },
+                                 vl);
+                float vf = 0.f;
+#pragma unroll
+                for (int l = 0; l < 7; ++l) vf += rp.f[l] * vl[0][l];
+                v = vf;
             } else {
                 v = 0.0;
                 for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * __ldg(S.T64 + (size_t)lm * S.n_shell + s);
@@ -2236,6 +2349,14 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                 int l = 0;
                 while ((l + 1) * (l + 1) <= tid) ++l;
                 sm.Qc[tid] = (float)(kFourPi / (2 * l + 1) * q);
+            }
+            __syncthreads();
+            if (tid < kNlm) {
+                int l = 0;
+                while ((l + 1) * (l + 1) <= tid) ++l;
+                const int i0 = l * l + l, mm = tid - i0;
+                sm.cq2[tid] = mm < 0 ? make_float2(0.f, 0.f)
+                                     : make_float2(sm.cn[tid] * sm.Qc[tid], mm > 0 ? sm.cn[tid] * sm.Qc[i0 - mm] : 0.f);
             }
             __syncthreads();
         }
