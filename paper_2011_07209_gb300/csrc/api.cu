@@ -114,6 +114,8 @@ struct exx_plan {
     OffsetSet off[2];
     SetLayout lay[2];
     int32_t *d_pe_m[2] = {}, *d_pe_off[2] = {}, *d_sh_m[2] = {}, *d_halo_off[2] = {}, *d_groups[2] = {};
+    int32_t *d_bnd[2] = {};
+    int n_bnd[2] = {};
     double *d_S64[2] = {}, *d_T64[2] = {};
     float *d_S32[2] = {}, *d_T32[2] = {};
     bool tables_valid = false;
@@ -293,6 +295,7 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_sh_m[s]);
         dev_free(p->d_halo_off[s]);
         dev_free(p->d_groups[s]);
+        dev_free(p->d_bnd[s]);
         dev_free(p->d_inv[s]);
         dev_free(p->d_gs_perm[s]);
         dev_free(p->d_gs_bstart[s]);
@@ -328,11 +331,14 @@ static int upload_layouts(exx_plan *p)
         dev_free(p->d_sh_m[s]);
         dev_free(p->d_halo_off[s]);
         dev_free(p->d_groups[s]);
+        dev_free(p->d_bnd[s]);
         dev_free(p->d_inv[s]);
         if ((e = dev_alloc(&p->d_pe_m[s], L.n_pe)) || (e = dev_alloc(&p->d_pe_off[s], L.n_pe)) ||
             (e = dev_alloc(&p->d_sh_m[s], L.n_shell)) || (e = dev_alloc(&p->d_halo_off[s], L.n_halo)) ||
-            (e = dev_alloc(&p->d_groups[s], L.groups.size())))
+            (e = dev_alloc(&p->d_groups[s], L.groups.size())) || (e = dev_alloc(&p->d_bnd[s], L.bnd.size())))
             return e;
+        p->n_bnd[s] = (int)L.bnd.size();
+        if (!L.bnd.empty()) CK(cudaMemcpy(p->d_bnd[s], L.bnd.data(), 4 * L.bnd.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(p->d_pe_m[s], L.pe_m.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(p->d_pe_off[s], L.pe_off.data(), 4 * L.n_pe, cudaMemcpyHostToDevice));
         if (L.n_shell) CK(cudaMemcpy(p->d_sh_m[s], L.sh_m.data(), 4 * L.n_shell, cudaMemcpyHostToDevice));
@@ -536,6 +542,8 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
         S.sh_m = p->d_sh_m[s];
         S.halo_off = p->d_halo_off[s];
         S.groups = p->d_groups[s];
+        S.bnd = p->d_bnd[s];
+        S.n_bnd = p->n_bnd[s];
         S.n_groups = (int)L.groups.size();
         for (int d = 0; d < 6; ++d) {
             S.rstride[d] = L.rstride[d];

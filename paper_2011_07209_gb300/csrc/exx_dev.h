@@ -59,6 +59,8 @@ struct SetDev {
     const int32_t *halo_off;       // [n_halo] dense-box offsets
     const int32_t *groups;         // [n_groups] aligned 4-point groups: (offset/4) << 4 | PE mask
     int n_groups;
+    const int32_t *bnd;            // [n_bnd] PE points with a halo point within the stencil's reach
+    int n_bnd;
     int rstride[6];                // dstride without the last-axis component
     int d2[6];                     // last-axis component of each direction
     // radial bins of the PE points (multipole starting guess): points sorted by bin

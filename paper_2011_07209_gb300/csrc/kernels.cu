@@ -430,34 +430,66 @@ __device__ __forceinline__ float2 dw_split(double x)
     return make_float2(h, (float)(x - (double)h));
 }
 
+// Running sum of products of double-float pairs: s is the FP32 sum of the
+// leading products w.hi x.hi, c (FP32) collects their exact rounding errors
+// (TwoSum, and the FMA error of each product) and the cross terms w.hi x.lo +
+// w.lo x.hi.  Error a few 2^-46 of the sum of the terms' magnitudes, in about a
+// third of the operations of renormalised double-float arithmetic.
+struct DfSum {
+    float s, c;
+    __device__ __forceinline__ void add_prod(float2 w, float2 x)
+    {
+        const float p = __fmul_rn(w.x, x.x);
+        const float e = __fmaf_rn(w.x, x.x, -p);
+        const float2 t = two_sum(s, p);
+        s = t.x;
+        c = __fadd_rn(c, __fadd_rn(__fadd_rn(t.y, e), __fmaf_rn(w.x, x.y, __fmul_rn(w.y, x.x))));
+    }
+    __device__ __forceinline__ void add(float2 x)
+    {
+        const float2 t = two_sum(s, x.x);
+        s = t.x;
+        c = __fadd_rn(c, __fadd_rn(t.y, x.y));
+    }
+};
+// a + b of two double-float pairs as an unnormalised pair: the high parts'
+// exact sum, the low parts added in FP32
+__device__ __forceinline__ float2 pair_sum(float2 a, float2 b)
+{
+    const float2 t = two_sum(a.x, b.x);
+    return make_float2(t.x, __fadd_rn(__fadd_rn(t.y, a.y), b.y));
+}
+
 // r = 4 pi rho + L v on PE in double-float arithmetic: v as (hi, lo) pairs in
-// the dense box, 4 pi rho as pairs per PE point, stencil weights as pairs.  The
-// error is a few 2^-48 of the sum of the magnitudes of the stencil terms (FP64:
-// 2^-53), far below the CG tolerance times |b|.  r is stored rounded to FP32,
-// the precision of the inner solve it restarts; returns sum r^2 in FP64.
+// the dense box, 4 pi rho as pairs per PE point, stencil weights as pairs, the
+// terms summed by DfSum.  The error is a few 2^-46 of the sum of the magnitudes
+// of the stencil terms (FP64: 2^-53), far below the CG tolerance times |b|.  r
+// is stored rounded to FP32, the precision of the inner solve it restarts;
+// returns sum r^2 (per thread in double-float, over the CTA in FP64).
 template <int FDN>
 __device__ __noinline__ double residual_df(const SetDev &S, const float2 *vb, const float2 *__restrict__ b2,
                                            float *__restrict__ r32, const float2 (*cw)[8], float2 center,
                                            const int *ds, int ndir, double *red)
 {
-    double acc[1] = {0.0};
+    DF a2 = {0.f, 0.f};
     for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
         const int off = S.pe_off[k];
-        float2 a = dw_mul(center, vb[off]);
+        DfSum a = {0.f, 0.f};
+        a.add_prod(center, vb[off]);
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
             if (d < ndir) {
                 const int st = ds[d];
 #pragma unroll
-                for (int s_ = 1; s_ <= FDN; ++s_)
-                    a = dw_add(a, dw_mul(cw[d][s_], dw_add(vb[off + s_ * st], vb[off - s_ * st])));
+                for (int s_ = 1; s_ <= FDN; ++s_) a.add_prod(cw[d][s_], pair_sum(vb[off + s_ * st], vb[off - s_ * st]));
             }
         }
-        a = dw_add(a, b2[k]);
-        const float r = __fadd_rn(a.x, a.y);
+        a.add(b2[k]);
+        const float r = __fadd_rn(a.s, a.c);
         r32[k] = r;
-        acc[0] += (double)r * (double)r;
+        df_fma(a2, r, r);
     }
+    double acc[1] = {(double)a2.hi + (double)a2.lo};
     block_sum<1>(acc, red);
     return acc[0];
 }
@@ -2092,12 +2124,17 @@ struct PairBox {
 // (v as double-float pairs), the stencil in FP32 and the sum in double-float.
 // Only the stopping threshold tol |b| uses it when the CG starts from the
 // multipole guess, whose residual (double-float) is the CG's first residual.
+// L v vanishes at PE points without a halo point in the stencil's reach, so
+// the caller passes each thread's part of sum (4 pi rho)^2 over all PE points
+// (init, taken in the density pass) and only the boundary points are visited
+// here, replacing (4 pi rho)^2 by b^2.
 __device__ __noinline__ double bnorm2_f32(const SetDev &S, const float2 *__restrict__ vb,
                                           const float2 *__restrict__ b2, const float (*cw)[8], float center,
-                                          const int *ds, int ndir, int fdn, float2 *red2)
+                                          const int *ds, int ndir, int fdn, float2 *red2, float2 init)
 {
-    DF a[1] = {{0.f, 0.f}};
-    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+    DF a[1] = {{init.x, init.y}};
+    for (int j = threadIdx.x; j < S.n_bnd; j += blockDim.x) {
+        const int k = __ldg(S.bnd + j);
         const int off = S.pe_off[k];
         float acc = center * vb[off].x;
 #pragma unroll
@@ -2110,8 +2147,9 @@ __device__ __noinline__ double bnorm2_f32(const SetDev &S, const float2 *__restr
             }
         }
         const float2 q = b2[k];
-        const float b = (q.x + acc) + q.y;
+        const float b = (q.x + acc) + q.y, b0 = q.x + q.y;
         df_fma(a[0], b, b);
+        df_fma(a[0], -b0, b0);
     }
     block_sum_df<1>(a, red2);
     // block_sum_df leaves the total in warp 0: broadcast it
@@ -2193,6 +2231,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
     __shared__ SmemCell sm;
     __shared__ double red[33 * 10 + 64];
     __shared__ double qpart[kSolveThreads / 32][kNlm];
+    __shared__ float2 s_bpart[kSolveThreads];   // per thread: sum (4 pi rho)^2 of its PE points
     __shared__ int s_pair, s_cell, s_flag;
 
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -2283,14 +2322,21 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             const size_t bvol = (size_t)C.box[0] * C.box[1] * C.box[2];
             const double *__restrict__ phi_i = C.phi + (size_t)pr.i * bvol;
             const double *__restrict__ phi_j = C.phi + (size_t)pr.j * bvol;
+            DF bq = {0.f, 0.f};   // this thread's part of sum (4 pi rho)^2 (bnorm2_f32)
             for (int k = tid; k < S.n_pe; k += nt) {
                 int m0, m1, m2;
                 unpack_m(__ldg(S.pe_m + k), m0, m1, m2);
                 const long long a = fi.at(C, C.box, m0, m1, m2), b = fj.at(C, C.box, m0, m1, m2);
                 const double rk = (a >= 0 ? __ldg(phi_i + a) : 0.0) * (b >= 0 ? __ldg(phi_j + b) : 0.0);
                 rho[k] = rk;
-                if (dfm) b2[k] = dw_split(kFourPi * rk);
+                if (dfm) {
+                    const float2 bb = dw_split(kFourPi * rk);
+                    b2[k] = bb;
+                    const float bf = bb.x + bb.y;
+                    df_fma(bq, bf, bf);
+                }
             }
+            s_bpart[tid] = make_float2(bq.hi, bq.lo);
         }
         __syncthreads();
 
@@ -2381,7 +2427,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
         // will start from the multipole guess (no warm start), only |b| is needed here
         const bool b_only = dfm && C.guess && S.gs_perm && !C.warm_map;
         double rr2 = b_only ? bnorm2_f32(S, vb, b2, sm.cw32, sm.center32, sm.ds, ndir, fdn,
-                                         reinterpret_cast<float2 *>(red))
+                                         reinterpret_cast<float2 *>(red), s_bpart[tid])
                             : residual();
         const double bn = sqrt(rr2);
         const double stop = C.tol * bn;

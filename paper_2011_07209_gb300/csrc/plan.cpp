@@ -469,7 +469,10 @@ int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L)
                 if (!s) continue;
                 const long long id = mindex(m[0] + s * st.dir[d][0], m[1] + s * st.dir[d][1], m[2] + s * st.dir[d][2]);
                 if (id < 0 || memb[id] == 0) return EXX_ERR_HALO;
-                if (memb[id] == 2) is_halo[shell_idx[id]] = 1;
+                if (memb[id] == 2) {
+                    is_halo[shell_idx[id]] = 1;
+                    if (L.bnd.empty() || L.bnd.back() != q) L.bnd.push_back(q);
+                }
             }
     }
     auto box_off = [&](const int *m) -> int32_t {

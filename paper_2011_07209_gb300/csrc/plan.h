@@ -74,6 +74,7 @@ struct SetLayout {
     std::vector<int32_t> pe_m, pe_off;     // packed offsets and box offsets of PE points
     std::vector<int32_t> sh_m, halo_off;   // packed offsets of shell points; box offsets of halo points
     std::vector<int32_t> groups;           // aligned 4-point groups covering PE
+    std::vector<int32_t> bnd;              // PE points with a halo point within the stencil's reach, ascending
     int rstride[6] = {};                   // box stride of a direction without its last-axis part
 };
 int make_layout(const OffsetSet &o, const Stencil &st, int fd_n, SetLayout &L);
