@@ -281,7 +281,9 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         }
     }
     G.floats = off;
-    if ((e = mg_put(p, s, T.cinv, &G.cinv)) || (e = mg_put(p, s, T.pinfo, &G.pinfo))) return e;
+    if ((e = mg_put(p, s, T.cinv, &G.cinv)) || (e = mg_put(p, s, T.pinfo, &G.pinfo)) ||
+        (e = mg_put(p, s, T.pinfo1, &G.pinfo1)))
+        return e;
     if ((e = dev_alloc(&p->d_mg[s], 1))) return e;
     CK(cudaMemcpy(p->d_mg[s], &G, sizeof(MgDev), cudaMemcpyHostToDevice));
     return EXX_OK;

@@ -44,6 +44,7 @@ struct MgDev {
     int kmap[kMgLevelsDev][125];       // window position -> pattern entry, -1 outside the pattern
     const float *cinv;             // [n][n] inverse of the coarsest operator, row-major
     const int32_t *pinfo;          // [fine groups] level-1 parents row << 2 | (u0 & 1) << 1 | (u1 & 1)
+    const int32_t *pinfo1;         // [level-1 runs] the same onto level 2 (null below three levels)
 };
 
 // Geometry of one subdomain kind (self pairs or non-self pairs) of one cell.

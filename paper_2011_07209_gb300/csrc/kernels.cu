@@ -1174,7 +1174,7 @@ struct MgSm {                      // the hierarchy of the pair's set, in shared
     const int32_t *pts[kMgLevelsDev];
     const float *wexp[kMgLevelsDev], *dinv[kMgLevelsDev], *dbox[kMgLevelsDev];
     const float *cinv;
-    const int32_t *pinfo;
+    const int32_t *pinfo, *pinfo1;
     int koff[kMgLevelsDev][kMgKDev];
     float wint[kMgLevelsDev][kMgKDev];
     int n_groups[kMgLevelsDev], n_pure[kMgLevelsDev];
@@ -1299,8 +1299,8 @@ __device__ __forceinline__ float mg_row(int l, int i, int o, const float *__rest
 // loads give the 12 values that the run's four points need (the same loads
 // serve all four), and the weights come from the interior stencil in shared
 // memory or, for runs with rows of their own, one float4 per window position.
-__device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const float *__restrict__ X,
-                                              float *__restrict__ T)
+__device__ __noinline__ void mg_resid_runs(const float *__restrict__ R, const float *__restrict__ X,
+                                              float *__restrict__ T, bool fold)
 {
     const MgSm &m = g_mg_sm;
     const int l = 1;
@@ -1328,7 +1328,7 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
             // one float4 of weights per window position for the run's four points
             const int nm = ng - npure;
             const float4 *__restrict__ wm = m.wmix[l] + (g - npure);
-#pragma unroll 5
+#pragma unroll 2
             for (int dxy = 0; dxy < 25; ++dxy) {
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
                 const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
@@ -1344,9 +1344,63 @@ __device__ __forceinline__ void mg_resid_runs(const float *__restrict__ R, const
                 }
             }
         }
+        const float ds = m.dscale;
+        const float *__restrict__ db = m.dbox[l];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            if (mask & (1 << i)) T[off + i] = R[off + i] - acc[i];
+            if (mask & (1 << i)) {
+                const float t = R[off + i] - acc[i];
+                T[off + i] = fold ? X[off + i] + ds * db[off + i] * t : t;
+            }
+    }
+}
+
+// Level 1 takes its post-smoothing inside the residual pass (T = X + D (R - A X),
+// the smoothed correction, goes to the T box): the V-cycle's level-1 result is
+// in T when the hierarchy has a level 2 and level 1 runs in the run form.
+__device__ __forceinline__ bool mg_fold1(const MgSm &m) { return m.nlev > 2 && m.n_groups[1] > 0; }
+
+// Z_1 = P Z_2 on the level-1 runs: a run's four points start at an even
+// last-axis coordinate, so they take their last-axis parents from three level-2
+// values of each (x, y) row, one row or two along each axis whose coordinate is
+// odd (pinfo1), as pass D does for the fine groups.
+__device__ __noinline__ void mg_prolong_runs1()
+{
+    const MgSm &m = g_mg_sm;
+    const int ng = m.n_groups[1];
+    const float *__restrict__ Z2 = m.Z[2];
+    float *__restrict__ Z1 = m.Z[1];
+    const int cB2 = m.Bp2[2], sx = m.Bp1[2] * m.Bp2[2];
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int32_t gw = __ldg(m.groups[1] + g);
+        const int off = (gw >> 4) << 2, mask = gw & 15;
+        const int32_t pinf = __ldg(m.pinfo1 + g);
+        const bool ox = pinf & 2, oy = pinf & 1;
+        const float *rb = Z2 + (pinf >> 2);
+        float c_0 = rb[0], c_1 = rb[1], c_2 = rb[2];
+        const float y0 = rb[cB2], y1 = rb[cB2 + 1], y2 = rb[cB2 + 2];
+        const float x0 = rb[sx], x1 = rb[sx + 1], x2 = rb[sx + 2];
+        const float xy0 = rb[sx + cB2], xy1 = rb[sx + cB2 + 1], xy2 = rb[sx + cB2 + 2];
+        if (oy) {
+            c_0 += y0;
+            c_1 += y1;
+            c_2 += y2;
+        }
+        if (ox) {
+            c_0 += x0;
+            c_1 += x1;
+            c_2 += x2;
+        }
+        if (ox && oy) {
+            c_0 += xy0;
+            c_1 += xy1;
+            c_2 += xy2;
+        }
+        const float wxy = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+        const float z[4] = {wxy * c_0, wxy * 0.5f * (c_0 + c_1), wxy * c_1, wxy * 0.5f * (c_1 + c_2)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (mask & (1 << i)) Z1[off + i] = z[i];
     }
 }
 
@@ -1460,6 +1514,14 @@ __device__ __noinline__ void mg_coarse_cycle()
         const float *R = m.R[l];
         float *Z = m.Z[l], *T = m.T[l];
         const float ds = m.dscale;
+        if (l == 1 && mg_fold1(m)) {
+            // Z_1 = P Z_2 by runs, then T_1 = Z_1 + D_1 (R_1 - A_1 Z_1): the level's result
+            mg_prolong_runs1();
+            __syncthreads();
+            mg_resid_runs(R, Z, T, true);
+            __syncthreads();
+            break;
+        }
         for (int i = tid; i < m.n[l]; i += nt) {
             const int o = pts[i];
             int u0, u1, u2;
@@ -1468,7 +1530,7 @@ __device__ __noinline__ void mg_coarse_cycle()
                    mg_prolong_at(m, l, u0 - kMgPadDev, u1 - kMgPadDev, u2 - kMgPadDev);
         }
         __syncthreads();
-        if (l == 1 && m.n_groups[1] > 0) mg_resid_runs(R, Z, T);
+        if (l == 1 && m.n_groups[1] > 0) mg_resid_runs(R, Z, T, false);
         else mg_resid(l, R, Z, T);
         __syncthreads();
         for (int i = tid; i < m.n[l]; i += nt) {
@@ -1602,7 +1664,7 @@ __device__ __noinline__ float2 mg_pass_d(const SetDev &S, const SmemCell &sm, co
     const MgSm &m = g_mg_sm;
     const int32_t *__restrict__ grp = S.groups;
     const int32_t *__restrict__ pinfo = m.pinfo;
-    const float *__restrict__ Z1 = m.Z[1];
+    const float *__restrict__ Z1 = mg_fold1(m) ? m.T[1] : m.Z[1];   // the level-1 result of the cycle
     const int cB2 = m.Bp2[1], sx = m.Bp1[1] * m.Bp2[1];
     DF a = {0.f, 0.f};
     front_sweep(
@@ -1695,6 +1757,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             m.dscale = (float)(om / (double)G.omega);
             m.cinv = G.cinv;
             m.pinfo = G.pinfo;
+            m.pinfo1 = G.pinfo1;
             for (int l = 1; l < G.nlev; ++l) {
                 const MgLevelDev &v = G.lv[l];
                 m.n[l] = v.n;

@@ -956,6 +956,19 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             r.pinfo[g] = (int32_t)(base << 2 | (u[0] & 1) << 1 | (u[1] & 1));
         }
     }
+    if (nl >= 3) {
+        r.pinfo1.resize(r.groups[1].size());
+        for (size_t g = 0; g < r.groups[1].size(); ++g) {
+            int u[3];
+            coords(r.Bp[1], (long long)(r.groups[1][g] >> 4) << 2, u);
+            for (int a = 0; a < 3; ++a) u[a] -= kMgPad;
+            if (u[2] & 1) return EXX_ERR_ARG;   // runs start at an even coordinate (possibly -2, in the margin)
+            const long long base =
+                (((long long)(u[0] >> 1) + kMgPad) * r.Bp[2][1] + (u[1] >> 1) + kMgPad) * r.Bp[2][2] + (u[2] >> 1) + kMgPad;
+            if (u[0] < 0 || u[1] < 0 || base >= (1LL << 29)) return EXX_ERR_ARG;
+            r.pinfo1[g] = (int32_t)(base << 2 | (u[0] & 1) << 1 | (u[1] & 1));
+        }
+    }
     t = std::move(r);
     return EXX_OK;
 }

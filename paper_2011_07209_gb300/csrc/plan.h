@@ -153,6 +153,9 @@ struct MgTables {
     // by 2, with u0 & 1 in bit 1 and u1 & 1 in bit 0 (odd rows also read the
     // next level-1 row along that axis)
     std::vector<int32_t> pinfo;
+    // the same for the level-1 runs (groups[1], unpadded coordinates) onto level 2
+    // (a run starts at an even last-axis coordinate too); empty below three levels
+    std::vector<int32_t> pinfo1;
     long long slot_floats = 0;                      // three boxes per coarse level
 };
 int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t);

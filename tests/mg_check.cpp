@@ -354,7 +354,7 @@ int main(int argc, char **argv)
     MgTables T;
     if (make_mg_tables(L, st, 3, 200, 0.8, T)) return 5;
     int k2 = -1, n_exp1 = 0;
-    double rel2 = 1.0, runs_rel = 1.0, rruns_rel = 1.0, pinfo_rel = 1.0;
+    double rel2 = 1.0, runs_rel = 1.0, rruns_rel = 1.0, pinfo_rel = 1.0, pinfo1_rel = 1.0;
     bool aligned = true;
     if (T.nlev >= 2) {
         std::vector<MgLevel> lv2;
@@ -477,6 +477,45 @@ int main(int argc, char **argv)
                 }
                 pinfo_rel = dd / nn;
             }
+            // the level-2 -> level-1 prolongation by level-1 runs (pinfo1)
+            if (T.nlev >= 3) {
+                std::vector<float> z2(T.box[2], 0.f);
+                for (int i = 0; i < T.n[2]; ++i) {
+                    st_ = st_ * 1664525u + 1013904223u;
+                    z2[T.pts[2][i]] = (float)((st_ >> 8) * (1.0 / 16777216.0) - 0.5);
+                }
+                if (T.pinfo1.size() != T.groups[1].size()) pinfo1_rel = 1.0;
+                else {
+                    dd = nn = 0.0;
+                    const long long sx = (long long)T.Bp[2][1] * T.Bp[2][2], sy = T.Bp[2][2];
+                    for (size_t g = 0; g < T.groups[1].size(); ++g) {
+                        const long long off = (long long)(T.groups[1][g] >> 4) << 2;
+                        const int mask = T.groups[1][g] & 15;
+                        const int pi = T.pinfo1[g];
+                        const bool ox = pi & 2, oy = pi & 1;
+                        const long long b = pi >> 2;
+                        float c[3];
+                        for (int k = 0; k < 3; ++k) {
+                            c[k] = z2[b + k];
+                            if (oy) c[k] += z2[b + sy + k];
+                            if (ox) c[k] += z2[b + sx + k];
+                            if (ox && oy) c[k] += z2[b + sx + sy + k];
+                        }
+                        const float wxy = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+                        const float zv[4] = {wxy * c[0], wxy * 0.5f * (c[0] + c[1]), wxy * c[1],
+                                             wxy * 0.5f * (c[1] + c[2])};
+                        for (int i = 0; i < 4; ++i) {
+                            if (!(mask & (1 << i))) continue;
+                            int u[3];
+                            mt.coords(1, off + i, u);
+                            const double ref = mt.prolong_at(1, z2, u);
+                            dd = std::fmax(dd, std::fabs((double)zv[i] - ref));
+                            nn = std::fmax(nn, std::fabs(ref));
+                        }
+                    }
+                    pinfo1_rel = dd / nn;
+                }
+            }
         }
     }
     double d = 0.0, nx = 0.0;
@@ -492,8 +531,8 @@ int main(int argc, char **argv)
                 "\"level1_max_nnz\": %d, \"tables_levels\": %d, \"tables_pcg_iter\": %d, "
                 "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d, "
                 "\"runs_rel_diff\": %.3e, \"restrict_runs_rel_diff\": %.3e, \"restrict_runs_aligned\": %d, "
-                "\"prolong_groups_rel_diff\": %.3e}\n",
+                "\"prolong_groups_rel_diff\": %.3e, \"prolong_runs1_rel_diff\": %.3e}\n",
                 2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1],
-                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel);
+                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel, pinfo1_rel);
     return 0;
 }
