@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "exx_dev.h"
 #include "kernels.h"
@@ -467,7 +468,7 @@ __device__ __forceinline__ float2 pair_sum(float2 a, float2 b)
 // is stored rounded to FP32, the precision of the inner solve it restarts;
 // returns sum r^2 (per thread in double-float, over the CTA in FP64).
 template <int FDN>
-__device__ __noinline__ double residual_df(const SetDev &S, const float2 *vb, const float2 *__restrict__ b2,
+__device__ __noinline__ double residual_df(const SetDev &S, const float2 *__restrict__ vb, const float2 *__restrict__ b2,
                                            float *__restrict__ r32, const float2 (*cw)[8], float2 center,
                                            const int *ds, int ndir, double *red)
 {
@@ -510,13 +511,14 @@ __device__ __forceinline__ double residual_df_n(int fdn, const SetDev &S, const 
 // d_b v the central first difference along lattice axis b (weights w1).  Every
 // product and sum in double-float; in thread 0, out[0] = sum rho v and
 // out[1 + 3 b + alpha] = sum m_alpha rho d_b v (no dV).
-__device__ __noinline__ void energy_stress_df(const SetDev &S, const float2 (*w1)[8], const float2 *vb,
+__device__ __noinline__ void energy_stress_df(const SetDev &S, const float2 (*w1)[8], const float2 *__restrict__ vb,
                                               const float2 *__restrict__ b2, bool want_sigma, int fdn, float2 *red2,
                                               double *out)
 {
     DF acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = {0.f, 0.f};
+#pragma unroll 2
     for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
         const int off = S.pe_off[k];
         const float2 b = b2[k];
@@ -2238,24 +2240,68 @@ __device__ __noinline__ bool d_scatter(const SetDev &S, const SmemCell &sm, cons
     double *dx_i = C.dxx + (size_t)pr.i * dvol;
     double *dx_j = C.dxx + (size_t)pr.j * dvol;
     bool ok = true;
-    for (int k = threadIdx.x; k < S.n_pe + S.n_shell; k += blockDim.x) {
-        int m0, m1, m2;
-        double v;
-        if (k < S.n_pe) {
-            unpack_m(__ldg(S.pe_m + k), m0, m1, m2);
-            v = vbox[__ldg(S.pe_off + k)];
-        } else {
-            const int s = k - S.n_pe;
-            const int32_t pm = __ldg(S.sh_m + s);
-            unpack_m(pm, m0, m1, m2);
+    // U points per thread and step: their values, then their orbital values, then
+    // the atomics, so that the loads of all U points are in flight together
+    auto scatter = [&](auto U, const int *m, const double *v, const bool *live) {
+        constexpr int u_n = decltype(U)::value;
+        double f[u_n], g[u_n];
+#pragma unroll
+        for (int u = 0; u < u_n; ++u) {
+            const long long a = live[u] ? fj.at(C, C.box, m[3 * u], m[3 * u + 1], m[3 * u + 2]) : -1;
+            f[u] = a >= 0 ? __ldg(phi_j + a) : 0.0;
+            const long long b = (live[u] && !self) ? fi.at(C, C.box, m[3 * u], m[3 * u + 1], m[3 * u + 2]) : -1;
+            g[u] = b >= 0 ? __ldg(phi_i + b) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < u_n; ++u) {
+            if (!live[u]) continue;
+            const double val = v[u] * f[u];
+            const long long d = di.at(C, C.dbox, m[3 * u], m[3 * u + 1], m[3 * u + 2]);
+            if (d >= 0) atomicAdd(dx_i + d, val);
+            else ok &= val == 0.0;
+            if (!self) {
+                const double val2 = v[u] * g[u];
+                const long long d2 = dj.at(C, C.dbox, m[3 * u], m[3 * u + 1], m[3 * u + 2]);
+                if (d2 >= 0) atomicAdd(dx_j + d2, val2);
+                else ok &= val2 == 0.0;
+            }
+        }
+    };
+    const int nt = blockDim.x, npe = S.n_pe, nsh = S.n_shell;
+    constexpr int kUpe = 2, kUsh = 1;
+    for (int k0 = threadIdx.x; k0 < npe; k0 += kUpe * nt) {
+        int m[3 * kUpe];
+        double v[kUpe];
+        bool live[kUpe];
+#pragma unroll
+        for (int u = 0; u < kUpe; ++u) {
+            const int k = k0 + u * nt;
+            live[u] = k < npe;
+            const int kk = live[u] ? k : k0;
+            unpack_m(__ldg(S.pe_m + kk), m[3 * u], m[3 * u + 1], m[3 * u + 2]);
+            v[u] = vbox[__ldg(S.pe_off + kk)];
+        }
+        scatter(std::integral_constant<int, kUpe>(), m, v, live);
+    }
+    for (int s0 = threadIdx.x; s0 < nsh; s0 += kUsh * nt) {
+        int m[3 * kUsh];
+        double v[kUsh];
+        bool live[kUsh];
+#pragma unroll
+        for (int u = 0; u < kUsh; ++u) {
+            const int s = s0 + u * nt;
+            live[u] = s < nsh;
+            const int ss = live[u] ? s : s0;
+            const int32_t pm = __ldg(S.sh_m + ss);
+            unpack_m(pm, m[3 * u], m[3 * u + 1], m[3 * u + 2]);
             if (mixed) {
                 float x, y, z;
                 xyz_of(sm.hf, pm, x, y, z);
                 const RinvPows rp(rsqrtf(x * x + y * y + z * z));
                 float vl[1][7];
                 solid_parts32<1>(x, y, z, C.lmax,
-                                 [&](int l, int m, float *k) {
-                                     const float2 c = sm.cq2[l * l + l + m];
+                                 [&](int l, int mm, float *k) {
+                                     const float2 c = sm.cq2[l * l + l + mm];
                                      k[0] = c.x;
                                      k[1] = c.y;
                                  },
@@ -2263,26 +2309,14 @@ __device__ __noinline__ bool d_scatter(const SetDev &S, const SmemCell &sm, cons
                 float vf = 0.f;
 #pragma unroll
                 for (int l = 0; l < 7; ++l) vf += rp.f[l] * vl[0][l];
-                v = vf;
+                v[u] = vf;
             } else {
-                v = 0.0;
-                for (int lm = 0; lm < kNlm; ++lm) v += sm.Q[lm] * __ldg(S.T64 + (size_t)lm * S.n_shell + s);
+                double w = 0.0;
+                for (int lm = 0; lm < kNlm; ++lm) w += sm.Q[lm] * __ldg(S.T64 + (size_t)lm * nsh + ss);
+                v[u] = w;
             }
         }
-        {
-            const long long a = fj.at(C, C.box, m0, m1, m2);
-            const double val = v * (a >= 0 ? __ldg(phi_j + a) : 0.0);
-            const long long d = di.at(C, C.dbox, m0, m1, m2);
-            if (d >= 0) atomicAdd(dx_i + d, val);
-            else ok &= val == 0.0;
-        }
-        if (!self) {
-            const long long a = fi.at(C, C.box, m0, m1, m2);
-            const double val = v * (a >= 0 ? __ldg(phi_i + a) : 0.0);
-            const long long d = dj.at(C, C.dbox, m0, m1, m2);
-            if (d >= 0) atomicAdd(dx_j + d, val);
-            else ok &= val == 0.0;
-        }
+        scatter(std::integral_constant<int, kUsh>(), m, v, live);
     }
     return ok;
 }
