@@ -137,6 +137,7 @@ struct exx_plan {
     int32_t *d_gs_perm[2] = {}, *d_gs_bstart[2] = {};   // radial bins of the starting guess
     uint8_t *d_gs_bin[2] = {};
     float *d_gs_S32[2] = {};
+    int4 *d_gs_info[2] = {};   // radius-sorted packed offset, box offset, bin, PE index
     // row partitions for the cluster path (mixed precision)
     ClusterPart cpart[2];
     bool cl_ok[2] = {false, false};
@@ -193,6 +194,10 @@ static bool simple_cubic(const exx_cell &c)
 }
 
 constexpr double kMgOmega = 0.8;   // weighted-Jacobi smoothing of the multigrid V-cycle
+#ifndef EXX_MG_DROP
+#define EXX_MG_DROP 0.005
+#endif
+constexpr double kMgDrop = EXX_MG_DROP;   // coarse-operator entries below this x the diagonal are lumped into it
 constexpr int kMaxBatchCells = 64;  // cells of one exx_pairs_solve_batch call
 
 static void free_mg(exx_plan *p, int s)
@@ -241,7 +246,7 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         return EXX_OK;
     }
     MgTables T;
-    int e = make_mg_tables(L, p->stencil, p->params.fd_order, 200, kMgOmega, T);
+    int e = make_mg_tables(L, p->stencil, p->params.fd_order, 200, kMgOmega, kMgDrop, T);
     if (e) return e;
     if (T.nlev < 2) return EXX_OK;
     MgDev &G = p->h_mg[s];
@@ -275,6 +280,8 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
             G.wdense[l][k] = T.wdense[l][k];
             G.kmap[l][k] = T.kmap[l][k];
         }
+        G.nrow[l] = T.nrow[l];
+        for (int k = 0; k < 25; ++k) G.rows[l][k] = T.rows[l][k];
         for (int k = 0; k < T.K[l]; ++k) {
             G.kd[l][k] = T.kd[l][k];
             G.wint[l][k] = T.wint[l][k];
@@ -303,6 +310,7 @@ static void free_geometry(exx_plan *p)
         dev_free(p->d_gs_bstart[s]);
         dev_free(p->d_gs_bin[s]);
         dev_free(p->d_gs_S32[s]);
+        dev_free(p->d_gs_info[s]);
         dev_free(p->d_cl_cta[s]);
         dev_free(p->d_cl_rows[s]);
         dev_free(p->d_cl_grc[s]);
@@ -401,7 +409,7 @@ static int build_geometry(exx_plan *p)
             (e = dev_alloc(&p->d_T32[s], (size_t)(o.n_me - o.n_pe) * kNlm)) ||
             (e = dev_alloc(&p->d_gs_perm[s], (size_t)o.n_pe)) || (e = dev_alloc(&p->d_gs_bstart[s], kGuessBins + 1)) ||
             (e = dev_alloc(&p->d_gs_bin[s], (size_t)o.n_pe)) ||
-            (e = dev_alloc(&p->d_gs_S32[s], (size_t)o.n_pe * kNlm)))
+            (e = dev_alloc(&p->d_gs_S32[s], (size_t)o.n_pe * kNlm)) || (e = dev_alloc(&p->d_gs_info[s], (size_t)o.n_pe)))
             return e;
     }
     if ((e = upload_layouts(p))) return e;
@@ -555,6 +563,7 @@ static void fill_celldev(const exx_plan *p, CellDev &C)
         S.gs_bstart = p->d_gs_bstart[s];
         S.gs_bin = p->d_gs_bin[s];
         S.gs_S32 = p->d_gs_S32[s];
+        S.gs_info = p->d_gs_info[s];
         S.cl_cta = p->cl_ok[s] ? p->d_cl_cta[s] : nullptr;
         S.cl_rows = p->d_cl_rows[s];
         S.cl_grc = p->d_cl_grc[s];
@@ -1139,6 +1148,8 @@ int exx_pairs_solve_batch(exx_ctx *ctx, int n_cells, exx_plan *const *plans, con
             CK(launch_tables(ctx->d_cells + qi, s, L.n_pe + L.n_shell, p->d_S64[s], p->d_S32[s], p->d_T64[s],
                              p->d_T32[s], stream));
             CK(launch_gather_rows(p->d_S32[s], p->d_gs_perm[s], L.n_pe, p->d_gs_S32[s], stream));
+            CK(launch_guess_info(p->d_gs_perm[s], p->d_gs_bin[s], p->d_pe_m[s], p->d_pe_off[s], L.n_pe,
+                                 p->d_gs_info[s], stream));
         }
         p->tables_valid = true;
     }

@@ -42,6 +42,8 @@ struct MgDev {
     float wint[kMgLevelsDev][kMgKDev];
     float wdense[kMgLevelsDev][125];   // interior weights on the 5 x 5 x 5 window ((dx+2) * 5 + dy+2) * 5 + dz+2
     int kmap[kMgLevelsDev][125];       // window position -> pattern entry, -1 outside the pattern
+    int nrow[kMgLevelsDev];            // (dx, dy) rows of the window with pattern entries
+    int rows[kMgLevelsDev][25];        // as (dx + 2) * 5 + dy + 2, ascending
     const float *cinv;             // [n][n] inverse of the coarsest operator, row-major
     const int32_t *pinfo;          // [fine groups] level-1 parents row << 2 | (u0 & 1) << 1 | (u1 & 1)
     const int32_t *pinfo1;         // [level-1 runs] the same onto level 2 (null below three levels)
@@ -69,6 +71,7 @@ struct SetDev {
     const int32_t *gs_bstart;      // [kGuessBins + 1] first sorted point of each bin
     const uint8_t *gs_bin;         // [n_pe] bin of each PE point
     const float *gs_S32;           // [n_pe][kNlm] S32 rows in sorted order
+    const int4 *gs_info;           // [n_pe] in sorted order: packed offset, box offset, bin, PE index
     // row partition over a cluster of CTAs (cluster path; cl_cta == NULL: not available)
     const int32_t *cl_cta;         // [nc][8]: G0, G1, K0, K1, rows, p_floats
     const int32_t *cl_rows;        // [B0 * B1][2]: owner rank (-2 halo-only row, -1 unused), offset of column 0

@@ -790,6 +790,7 @@ __device__ __noinline__ void cg_mixed(const CgMixed &cg, int &iters, int &refine
 
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
@@ -1184,6 +1185,7 @@ struct MgSm {                      // the hierarchy of the pair's set, in shared
     const float4 *wmix[kMgLevelsDev];
     float wdense[125];             // the window weights and map of level 1 (the level of the run path)
     int kmap[125];
+    int nrow1, rows1[25];          // level 1: (dx, dy) rows of the window with pattern entries
     float cr[kMgCoarsestDev];
 };
 
@@ -1307,14 +1309,15 @@ __device__ __noinline__ void mg_resid_runs(const float *__restrict__ R, const fl
     const MgSm &m = g_mg_sm;
     const int l = 1;
     const int ng = m.n_groups[l], npure = m.n_pure[l];
-    const int B1 = m.Bp1[l], B2 = m.Bp2[l];
+    const int B1 = m.Bp1[l], B2 = m.Bp2[l], nrow = m.nrow1;
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
         const int32_t gw = __ldg(m.groups[l] + g);
         const int off = (gw >> 4) << 2, mask = gw & 15;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         if (g < npure) {
 #pragma unroll 5
-            for (int dxy = 0; dxy < 25; ++dxy) {
+            for (int rw = 0; rw < nrow; ++rw) {
+                const int dxy = m.rows1[rw];
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
                 const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
                 const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
@@ -1331,7 +1334,8 @@ __device__ __noinline__ void mg_resid_runs(const float *__restrict__ R, const fl
             const int nm = ng - npure;
             const float4 *__restrict__ wm = m.wmix[l] + (g - npure);
 #pragma unroll 2
-            for (int dxy = 0; dxy < 25; ++dxy) {
+            for (int rw = 0; rw < nrow; ++rw) {
+                const int dxy = m.rows1[rw];
                 const float *row = X + off + ((dxy / 5 - 2) * B1 + (dxy % 5 - 2)) * B2;
                 const float4 a = ld4(row - 4), b = ld4(row), c = ld4(row + 4);
                 const float x[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
@@ -1676,11 +1680,14 @@ __device__ __noinline__ float2 mg_pass_d(const SetDev &S, const SmemCell &sm, co
             const int off = (gw >> 4) << 2, mask = gw & 15;
             const int32_t pinf = __ldg(pinfo + g);
             const bool ox = pinf & 2, oy = pinf & 1;
+            // the parents' row offset is even (u2 / 2 + margin with u2 = 0 mod 4, rows
+            // of a multiple of 4): the first two of each row's three values are one float2
             const float *rb = Z1 + (pinf >> 2);
-            float c_0 = rb[0], c_1 = rb[1], c_2 = rb[2];
-            const float y0 = rb[cB2], y1 = rb[cB2 + 1], y2 = rb[cB2 + 2];
-            const float x0 = rb[sx], x1 = rb[sx + 1], x2 = rb[sx + 2];
-            const float xy0 = rb[sx + cB2], xy1 = rb[sx + cB2 + 1], xy2 = rb[sx + cB2 + 2];
+            const float2 r00 = ld2(rb), r01 = ld2(rb + cB2), r10 = ld2(rb + sx), r11 = ld2(rb + sx + cB2);
+            float c_0 = r00.x, c_1 = r00.y, c_2 = rb[2];
+            const float y0 = r01.x, y1 = r01.y, y2 = rb[cB2 + 2];
+            const float x0 = r10.x, x1 = r10.y, x2 = rb[sx + 2];
+            const float xy0 = r11.x, xy1 = r11.y, xy2 = rb[sx + cB2 + 2];
             if (oy) {
                 c_0 += y0;
                 c_1 += y1;
@@ -1785,6 +1792,8 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
             for (int k = tid; k < 125; k += nt) {
                 m.wdense[k] = G.wdense[1][k];
                 m.kmap[k] = G.kmap[1][k];
+                if (k < 25) m.rows1[k] = G.rows[1][k];
+                if (k == 0) m.nrow1 = G.nrow[1];
             }
         for (int l = 1; l < G.nlev; ++l)
             for (int k = tid; k < G.lv[l].K; k += nt) {
@@ -1838,11 +1847,12 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
         {
             const F32Scale sc = f32_scale(1.0 / Sc);
             DF a[1] = {{0.f, 0.f}};
+            // (e is zero here: the boxes start zero for every pair and each reliable
+            // update clears it)
             for (int k = tid; k < npe; k += nt) {
                 const int off = poff[k];
                 const float r = sc.apply(r32[k]);
                 rf[off] = r;
-                ef[off] = 0.f;
                 df_add(a[0], r * r);
             }
             block_sum_df<1>(a, red2);
@@ -2005,15 +2015,6 @@ __device__ __forceinline__ void xyz_of(const float (*h)[3], int32_t pm, float &x
     z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
 }
 
-__device__ __forceinline__ void pe_xyz(const SetDev &S, const float (*h)[3], int k, float &x, float &y, float &z)
-{
-    int m0, m1, m2;
-    unpack_m(S.pe_m[k], m0, m1, m2);
-    x = h[0][0] * m0 + h[0][1] * m1 + h[0][2] * m2;
-    y = h[1][0] * m0 + h[1][1] * m1 + h[1][2] * m2;
-    z = h[2][0] * m0 + h[2][1] * m1 + h[2][2] * m2;
-}
-
 // Multipole moments of rho per radial bin over the radius-sorted copy of the
 // solid-harmonic table (no atomics: the same sums on every run).  Each bin is
 // split into two halves of its sorted range; the 2 kGuessBins pieces, in order
@@ -2052,10 +2053,10 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
         float b0 = 0.f, b1 = 0.f;
         for (int x = k0; x < k1; x += 32) {
             const bool live = x + lane < k1;
-            const int kk = S.gs_perm[live ? x + lane : x];
-            const float rl = live ? (float)rho[kk] : 0.f;
+            const int4 inf = __ldg(S.gs_info + (live ? x + lane : x));
+            const float rl = live ? (float)rho[inf.w] : 0.f;
             float px, py, pz;
-            pe_xyz(S, h, kk, px, py, pz);
+            xyz_of(h, inf.x, px, py, pz);
             const float r2 = px * px + py * py + pz * pz;
             const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
             const int xq = min(32, k1 - x);
@@ -2073,7 +2074,7 @@ __device__ __noinline__ void bin_moments(const SetDev &S, const CellDev &C, cons
             }
             __syncwarp();
             float f0 = 0.f, f1 = 0.f;
-#pragma unroll 8
+#pragma unroll 16
             for (int q = 0; q < 32; ++q) {
                 const float rp = mw[q][7];
                 const float *row = S.gs_S32 + (size_t)(x + min(q, xq - 1)) * kNlm;   // rows in sorted order
@@ -2141,10 +2142,10 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
     __syncthreads();
     const int lmax = C.lmax;
     for (int j = tid; j < S.n_pe; j += nt) {
-        const int kk = S.gs_perm[j];
-        const float4 *Gb = G + (int)S.gs_bin[kk] * kNlm;
+        const int4 inf = __ldg(S.gs_info + j);
+        const float4 *Gb = G + inf.z * kNlm;
         float x, y, z;
-        xyz_of(hf, S.pe_m[kk], x, y, z);
+        xyz_of(hf, inf.x, x, y, z);
         const float r2 = x * x + y * y + z * z;
         const RinvPows rp(r2 > 0.f ? rsqrtf(r2) : 0.f);
         float vl[2][7];
@@ -2160,8 +2161,8 @@ __device__ __noinline__ void multipole_guess(const SetDev &S, const CellDev &C, 
         float v = 0.f;
 #pragma unroll
         for (int l = 0; l < 7; ++l) v += rp.f[l] * vl[0][l] + vl[1][l];
-        if (df) reinterpret_cast<float2 *>(vbox)[S.pe_off[kk]] = make_float2(v, 0.f);   // double-float pair
-        else vbox[S.pe_off[kk]] = (double)v;
+        if (df) reinterpret_cast<float2 *>(vbox)[inf.y] = make_float2(v, 0.f);   // double-float pair
+        else vbox[inf.y] = (double)v;
     }
 }
 
@@ -3599,6 +3600,24 @@ cudaError_t launch_gather_rows(const float *src, const int32_t *perm, int n, flo
 {
     const long long total = (long long)n * kNlm;
     if (total > 0) k_gather_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, perm, n, dst);
+    return cudaGetLastError();
+}
+
+__global__ void k_guess_info(const int32_t *__restrict__ perm, const uint8_t *__restrict__ bin,
+                             const int32_t *__restrict__ pe_m, const int32_t *__restrict__ pe_off, int n,
+                             int4 *__restrict__ info)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        const int k = perm[j];
+        info[j] = make_int4(pe_m[k], pe_off[k], (int)bin[k], k);
+    }
+}
+
+cudaError_t launch_guess_info(const int32_t *perm, const uint8_t *bin, const int32_t *pe_m, const int32_t *pe_off,
+                              int n, int4 *info, cudaStream_t s)
+{
+    if (n > 0) k_guess_info<<<(n + 255) / 256, 256, 0, s>>>(perm, bin, pe_m, pe_off, n, info);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,9 @@ cudaError_t launch_tables(const CellDev *cell, int which, int n_points, double *
                           float *T32, cudaStream_t s);
 // dst[j][:] = src[perm[j]][:] for rows of kNlm floats
 cudaError_t launch_gather_rows(const float *src, const int32_t *perm, int n, float *dst, cudaStream_t s);
+// info[j] = (pe_m, pe_off, bin, k) of PE point k = perm[j] (the radius-sorted order of the guess)
+cudaError_t launch_guess_info(const int32_t *perm, const uint8_t *bin, const int32_t *pe_m, const int32_t *pe_off,
+                              int n, int4 *info, cudaStream_t s);
 cudaError_t launch_pair_list(const CellDev *cells, int n_cells, int n_rows, const ListDev &L, cudaStream_t s);
 cudaError_t launch_solve(const CellDev *cells, const ListDev &L, const SolveSlots &slots, bool mixed,
                          int inner_shift, cudaStream_t s);

@@ -761,7 +761,8 @@ int make_mg_levels(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
 }
 
 // Device form of the hierarchy (see plan.h).
-int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t)
+int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, double drop,
+                   MgTables &t)
 {
     t = MgTables();
     std::vector<MgLevel> lv;
@@ -855,6 +856,16 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             wint.push_back(A.val[k]);
             ++K;
         }
+        // pattern entries kept on the device: |a| >= drop x the interior diagonal; a dropped
+        // entry of any row is added, as |a|, to that row's diagonal (the change is
+        // + |a| (e_i -+ e_j)(e_i -+ e_j)^T over each symmetric pair, so the operator stays
+        // symmetric positive definite)
+        int kc = -1;
+        for (int k = 0; k < K; ++k)
+            if (r.kd[l][k] == (2 | 2 << 3 | 2 << 6)) kc = k;
+        if (kc < 0) return EXX_OK;
+        std::vector<char> keep(K, 1);
+        for (int k = 0; k < K; ++k) keep[k] = k == kc || std::fabs(wint[k]) >= drop * std::fabs(wint[kc]);
         r.K[l] = K;
         // rows of A_l over the pattern; interior rows first, then the others
         std::vector<double> w((size_t)A.n * K, 0.0), diag(A.n, 0.0);
@@ -872,7 +883,37 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             if (!(diag[i] > 0.0)) return EXX_OK;
             for (int k = 0; k < K && same; ++k) same = std::fabs(wi[k] - wint[k]) <= 1e-12 * std::fabs(wint[k]);
             interior[i] = same;
+            for (int k = 0; k < K; ++k)
+                if (!keep[k]) {
+                    wi[kc] += std::fabs(wi[k]);
+                    wi[k] = 0.0;
+                }
+            diag[i] = wi[kc];
         }
+        // compact the pattern to the kept entries (row weights keep their order)
+        {
+            double dint = wint[kc];
+            for (int k = 0; k < K; ++k)
+                if (!keep[k]) dint += std::fabs(wint[k]);
+            int Kn = 0;
+            std::vector<int> nk(K, -1);
+            for (int k = 0; k < K; ++k)
+                if (keep[k]) {
+                    nk[k] = Kn;
+                    r.kd[l][Kn] = r.kd[l][k];
+                    r.wint[l][Kn] = (float)(k == kc ? dint : wint[k]);
+                    ++Kn;
+                }
+            for (int i = 0; i < A.n; ++i) {
+                double *wi = &w[(size_t)i * K];
+                for (int k = 0; k < K; ++k)
+                    if (nk[k] >= 0) wi[nk[k]] = wi[k];   // nk[k] <= k: in place, ascending
+            }
+            for (int k = Kn; k < K; ++k) r.kd[l][k] = 0, r.wint[l][k] = 0.f;
+            K = Kn;
+            r.K[l] = K;
+        }
+        const int Kw = (int)keep.size();   // row stride of w
         std::vector<int> order;
         for (int pass = 1; pass >= 0; --pass)
             for (int i = 0; i < A.n; ++i)
@@ -892,7 +933,7 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             r.dinv[l][q] = (float)(omega / diag[i]);
             r.dbox[l][(size_t)pts[q]] = r.dinv[l][q];
             if (q >= n_int)
-                for (int k = 0; k < K; ++k) r.wexp[l][(size_t)k * n_exp + (q - n_int)] = (float)w[(size_t)i * K + k];
+                for (int k = 0; k < K; ++k) r.wexp[l][(size_t)k * n_exp + (q - n_int)] = (float)w[(size_t)i * Kw + k];
         }
         r.pts[l] = std::move(pts);
         // dense interior stencil, window -> pattern map, and runs of 4 points
@@ -902,6 +943,12 @@ int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_poin
             const int pos = ((kd & 7) * 5 + ((kd >> 3) & 7)) * 5 + ((kd >> 6) & 7);   // (dx, dy, dz) + 2
             r.wdense[l][pos] = r.wint[l][k];
             r.kmap[l][pos] = k;
+        }
+        r.nrow[l] = 0;
+        for (int dxy = 0; dxy < 25; ++dxy) {
+            bool any = false;
+            for (int dz = 0; dz < 5; ++dz) any |= r.kmap[l][dxy * 5 + dz] >= 0;
+            if (any) r.rows[l][r.nrow[l]++] = dxy;
         }
         std::vector<int32_t> at((size_t)r.box[l], -1);
         for (int q = 0; q < A.n; ++q) at[(size_t)r.pts[l][q]] = q;

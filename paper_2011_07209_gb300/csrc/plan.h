@@ -147,6 +147,8 @@ struct MgTables {
     std::vector<float> wmix[kMgMaxLevels];
     float wdense[kMgMaxLevels][125] = {};           // interior stencil on the 5 x 5 x 5 window (dx, dy, dz)
     int kmap[kMgMaxLevels][125] = {};               // window position -> pattern entry k, -1 outside the pattern
+    int nrow[kMgMaxLevels] = {};                    // (dx, dy) rows of the window holding pattern entries
+    int rows[kMgMaxLevels][25] = {};                // as (dx + 2) * 5 + dy + 2, ascending
     std::vector<float> cinv;                        // [n][n] of the coarsest level
     // per aligned fine group (SetLayout::groups): the level-1 box offset of the
     // last-axis parents of its first point in the row (u0/2, u1/2), shifted left
@@ -158,7 +160,10 @@ struct MgTables {
     std::vector<int32_t> pinfo1;
     long long slot_floats = 0;                      // three boxes per coarse level
 };
-int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, MgTables &t);
+// drop: pattern entries below drop x the interior diagonal are left out of the
+// device operators of the coarse levels (each added, as |a|, to its row's diagonal)
+int make_mg_tables(const SetLayout &L, const Stencil &st, int fd_n, int min_points, double omega, double drop,
+                   MgTables &t);
 
 // Candidate schedules of the autotuner (exx_plan_autotune), in the order that
 // breaks ties: with a multigrid hierarchy, MG with omega 0.8, 0.7, 0.6, each

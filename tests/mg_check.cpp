@@ -352,10 +352,10 @@ int main(int argc, char **argv)
     const int k1 = pcg(A, b, &mg, 1e-9, x1);
     // the device tables of the same hierarchy, applied in FP32 as the solver does
     MgTables T;
-    if (make_mg_tables(L, st, 3, 200, 0.8, T)) return 5;
+    if (make_mg_tables(L, st, 3, 200, 0.8, 0.005, T)) return 5;
     int k2 = -1, n_exp1 = 0;
     double rel2 = 1.0, runs_rel = 1.0, rruns_rel = 1.0, pinfo_rel = 1.0, pinfo1_rel = 1.0;
-    bool aligned = true;
+    bool aligned = true, pinfo_even = true;
     if (T.nlev >= 2) {
         std::vector<MgLevel> lv2;
         make_mg_levels(L, st, 3, 200, lv2);
@@ -457,6 +457,7 @@ int main(int argc, char **argv)
                     const int pi = T.pinfo[g];
                     const bool ox = pi & 2, oy = pi & 1;
                     const long long b = pi >> 2;
+                    if ((b & 1) || (sy & 1) || (sx & 1)) pinfo_even = false;   // float2 reads of the parents
                     float c[3];
                     for (int k = 0; k < 3; ++k) {
                         c[k] = zc[b + k];
@@ -531,8 +532,8 @@ int main(int argc, char **argv)
                 "\"level1_max_nnz\": %d, \"tables_levels\": %d, \"tables_pcg_iter\": %d, "
                 "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d, "
                 "\"runs_rel_diff\": %.3e, \"restrict_runs_rel_diff\": %.3e, \"restrict_runs_aligned\": %d, "
-                "\"prolong_groups_rel_diff\": %.3e, \"prolong_runs1_rel_diff\": %.3e}\n",
+                "\"prolong_groups_rel_diff\": %.3e, \"prolong_runs1_rel_diff\": %.3e, \"pinfo_even\": %d}\n",
                 2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1],
-                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel, pinfo1_rel);
+                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel, pinfo1_rel, pinfo_even ? 1 : 0);
     return 0;
 }

@@ -54,5 +54,6 @@ def test_vcycle_preconditioned_cg(harness, cell, n_stcl):
     assert r["restrict_runs_rel_diff"] < 1e-5 and r["restrict_runs_aligned"] == 1
     # pass D's prolongation onto the fine groups (level-1 rows from the per-group table)
     assert r["prolong_groups_rel_diff"] < 1e-6
+    assert r["pinfo_even"] == 1                      # pass D reads each parents' row start as a float2
     # and level 2 onto the level-1 runs (pinfo1)
     assert r["prolong_runs1_rel_diff"] < 1e-6
