@@ -784,7 +784,7 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="trajectory256 under torchrun: the ranks share one cell's pairs (LPT partition, all-reduce "
                          "of E, sigma and D per step; strong scaling) instead of solving one cell each")
-    ap.add_argument("--autotune", type=int, default=304,
+    ap.add_argument("--autotune", type=int, default=1216,
                     help="autotune each plan's solver schedule on this many pairs first (0: the default schedule)")
     ap.add_argument("--workload", default="trajectory256", choices=["trajectory256", "water64"] + sorted(WORKLOADS),
                     help="trajectory256 is the headline workload; the others print their own line")
