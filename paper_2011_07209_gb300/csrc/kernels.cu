@@ -557,6 +557,83 @@ __device__ __noinline__ void energy_stress_df(const SetDev &S, const float2 (*w1
         for (int k = 0; k < 10; ++k) out[k] = ((double)acc[k].hi + (double)acc[k].lo) / kFourPi;
 }
 
+// The double-float residual of residual_df and, from the same loads, the Step V
+// sums of energy_stress_df (the stencil's first three directions are the lattice
+// axes, so v at +-s along each axis is already at hand).  Taken for the residual
+// that is expected to end the CG: when it does, the separate Step V pass is not
+// needed.  Returns sum r^2 in every thread; es_out (thread 0) as energy_stress_df.
+template <int FDN>
+__device__ __noinline__ double residual_es_df(const SetDev &S, const float2 *__restrict__ vb,
+                                              const float2 *__restrict__ b2, float *__restrict__ r32,
+                                              const float2 (*cw)[8], float2 center, const int *ds, int ndir,
+                                              double *red, const float2 (*w1)[8], bool want_sigma, double *es_out)
+{
+    DF a2 = {0.f, 0.f};
+    DF acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = {0.f, 0.f};
+    for (int k = threadIdx.x; k < S.n_pe; k += blockDim.x) {
+        const int off = S.pe_off[k];
+        const float2 v0 = vb[off];
+        DfSum a = {0.f, 0.f};
+        a.add_prod(center, v0);
+        float dd[3] = {0.f, 0.f, 0.f};   // first differences along the lattice axes (energy_stress_df)
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (d < ndir) {
+                const int st = ds[d];
+#pragma unroll
+                for (int s_ = 1; s_ <= FDN; ++s_) {
+                    const float2 vp = vb[off + s_ * st], vm = vb[off - s_ * st];
+                    a.add_prod(cw[d][s_], pair_sum(vp, vm));
+                    if (d < 3) dd[d] += w1[d][s_].x * ((vp.x - vm.x) + (vp.y - vm.y));
+                }
+            }
+        }
+        const float2 b = b2[k];
+        a.add(b);
+        const float r = __fadd_rn(a.s, a.c);
+        r32[k] = r;
+        df_fma(a2, r, r);
+        const float2 e = dw_mul(b, v0);
+        acc[0] = df_sum(acc[0], {e.x, e.y});
+        if (want_sigma) {
+            int m0, m1, m2;
+            unpack_m(S.pe_m[k], m0, m1, m2);
+            const float mf[3] = {(float)m0, (float)m1, (float)m2};
+#pragma unroll
+            for (int db = 0; db < 3; ++db) {
+                const float2 rd = dw_mul(b, make_float2(dd[db], 0.f));
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    const float2 p = two_prod(mf[al], rd.x);
+                    acc[1 + 3 * db + al] = df_sum(acc[1 + 3 * db + al], {p.x, __fmaf_rn(mf[al], rd.y, p.y)});
+                }
+            }
+        }
+    }
+    double rr[1] = {(double)a2.hi + (double)a2.lo};
+    block_sum<1>(rr, red);
+    block_sum_df<10>(acc, reinterpret_cast<float2 *>(red));
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 10; ++k) es_out[k] = ((double)acc[k].hi + (double)acc[k].lo) / kFourPi;
+    __syncthreads();
+    return rr[0];
+}
+__device__ __forceinline__ double residual_es_df_n(int fdn, const SetDev &S, const float2 *vb, const float2 *b2,
+                                                   float *r32, const float2 (*cw)[8], float2 center, const int *ds,
+                                                   int ndir, double *red, const float2 (*w1)[8], bool want_sigma,
+                                                   double *es_out)
+{
+    switch (fdn) {
+    case 1: return residual_es_df<1>(S, vb, b2, r32, cw, center, ds, ndir, red, w1, want_sigma, es_out);
+    case 2: return residual_es_df<2>(S, vb, b2, r32, cw, center, ds, ndir, red, w1, want_sigma, es_out);
+    case 3: return residual_es_df<3>(S, vb, b2, r32, cw, center, ds, ndir, red, w1, want_sigma, es_out);
+    default: return residual_es_df<4>(S, vb, b2, r32, cw, center, ds, ndir, red, w1, want_sigma, es_out);
+    }
+}
+
 // x * sc in FP32 for any FP64 scale sc (sc = m 2^e, x m rounded once, then an
 // exact power-of-two scaling), so that tiny residuals reach the O(1) frame.
 struct F32Scale {
@@ -1574,7 +1651,8 @@ __shared__ int g_mg_need[kMaxSweepChunks];   // update front of each chunk (mult
 struct MgScalars {
     double rz, rmax, S;
     float alpha, beta;
-    int act;   // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+    int act;    // 0 continue, 1 reliable update, 2 reliable update after a breakdown
+    int conv;   // the recursive residual predicts convergence (the reliable update may end the CG)
 };
 __shared__ MgScalars g_mg_cs;
 
@@ -1736,8 +1814,9 @@ __device__ __noinline__ float2 mg_pass_d(const SetDev &S, const SmemCell &sm, co
 // (pass B's t is discarded when its <r, r> calls for a reliable update).
 template <int FDN>
 __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mgbase, int &iters, int &refine,
-                                         int &status, double &rnorm)
+                                         int &status, double &rnorm, double *es, bool &es_done)
 {
+    es_done = false;
     const SetDev &S = *cg.S;
     const SmemCell &sm = *cg.sm;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -1900,6 +1979,7 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                     const double rr = (double)b[0].hi + (double)b[0].lo;
                     const double rn = sqrt(rr);
                     if (!(rn == rn) || rn <= inner_red * cs.rmax || rn * cs.S <= 0.5 * stop) cs.act = 1;
+                    cs.conv = rn * cs.S <= 0.5 * stop;
                 }
                 __syncthreads();
                 act = cs.act;
@@ -1915,8 +1995,17 @@ __device__ __noinline__ void cg_mixed_mg(const CgMixed &cg, float *zf, float *mg
                     ef[off] = 0.f;
                 }
                 __syncthreads();
-                rnorm = sqrt(residual_df_n(cg.fdn, S, vb, cg.b2, r32, sm.cwdf, sm.centerdf, sm.ds, ndir, cg.red));
-                if (rnorm <= stop) return;
+                // when the recursive residual predicts the end of the CG, the same pass
+                // takes the Step V sums
+                const bool conv = act == 1 && cs.conv;
+                rnorm = sqrt(conv ? residual_es_df_n(cg.fdn, S, vb, cg.b2, r32, sm.cwdf, sm.centerdf, sm.ds, ndir,
+                                                     cg.red, sm.w1df, sm.C.stress_mode != 2, es)
+                                  : residual_df_n(cg.fdn, S, vb, cg.b2, r32, sm.cwdf, sm.centerdf, sm.ds, ndir,
+                                                  cg.red));
+                if (rnorm <= stop) {
+                    es_done = conv;
+                    return;
+                }
                 if (!(rnorm == rnorm)) {
                     status = 5;
                     return;
@@ -2654,13 +2743,14 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
             cg.inner_red = C.inner_shift > 0 ? ldexp(1.0, -C.inner_shift) : inner_red;
             cg.b2 = b2;
             if (dfm) {
+                bool es_done = false;   // the CG's last residual pass took the Step V sums
                 if (C.precond && S.mg && fdn <= 3) {
                     float *zf = reinterpret_cast<float *>(slot + W.off_zf);
                     float *mgb = reinterpret_cast<float *>(slot + W.off_mg);
                     switch (fdn) {
-                    case 1: cg_mixed_mg<1>(cg, zf, mgb, iters, refine, status, rnorm); break;
-                    case 2: cg_mixed_mg<2>(cg, zf, mgb, iters, refine, status, rnorm); break;
-                    default: cg_mixed_mg<3>(cg, zf, mgb, iters, refine, status, rnorm); break;
+                    case 1: cg_mixed_mg<1>(cg, zf, mgb, iters, refine, status, rnorm, es, es_done); break;
+                    case 2: cg_mixed_mg<2>(cg, zf, mgb, iters, refine, status, rnorm, es, es_done); break;
+                    default: cg_mixed_mg<3>(cg, zf, mgb, iters, refine, status, rnorm, es, es_done); break;
                     }
                 } else {
                     switch (fdn) {
@@ -2671,8 +2761,10 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) k_pair_solve(c
                     }
                 }
                 __syncthreads();
-                // Step V integrals from the double-float solution
-                energy_stress_df(S, sm.w1df, vb, b2, C.stress_mode != 2, fdn, reinterpret_cast<float2 *>(red), es);
+                // Step V integrals from the double-float solution (unless the CG's last
+                // residual pass took them)
+                if (!es_done)
+                    energy_stress_df(S, sm.w1df, vb, b2, C.stress_mode != 2, fdn, reinterpret_cast<float2 *>(red), es);
                 // v back to FP64 on PE for D and the warm-start store
                 for (int k = tid; k < S.n_pe; k += nt) {
                     const int off = S.pe_off[k];
