@@ -198,6 +198,10 @@ constexpr double kMgOmega = 0.8;   // weighted-Jacobi smoothing of the multigrid
 #define EXX_MG_DROP 0.005
 #endif
 constexpr double kMgDrop = EXX_MG_DROP;   // coarse-operator entries below this x the diagonal are lumped into it
+#ifndef EXX_MG_MIN_POINTS
+#define EXX_MG_MIN_POINTS 200
+#endif
+constexpr int kMgMinPoints = EXX_MG_MIN_POINTS;   // coarsening stops at this many points (the coarsest is inverted)
 constexpr int kMaxBatchCells = 64;  // cells of one exx_pairs_solve_batch call
 
 static void free_mg(exx_plan *p, int s)
@@ -246,7 +250,7 @@ static int upload_mg(exx_plan *p, int s, const SetLayout &L)
         return EXX_OK;
     }
     MgTables T;
-    int e = make_mg_tables(L, p->stencil, p->params.fd_order, 200, kMgOmega, kMgDrop, T);
+    int e = make_mg_tables(L, p->stencil, p->params.fd_order, kMgMinPoints, kMgOmega, kMgDrop, T);
     if (e) return e;
     if (T.nlev < 2) return EXX_OK;
     MgDev &G = p->h_mg[s];
