@@ -355,7 +355,9 @@ int main(int argc, char **argv)
     if (make_mg_tables(L, st, 3, 200, 0.8, 0.005, T)) return 5;
     int k2 = -1, n_exp1 = 0;
     double rel2 = 1.0, runs_rel = 1.0, rruns_rel = 1.0, pinfo_rel = 1.0, pinfo1_rel = 1.0;
-    bool aligned = true, pinfo_even = true;
+    bool aligned = true, pinfo_even = true, coarse_spd = true;
+    double coarse_asym = 0.0;
+    int coarse_checked = 0;
     if (T.nlev >= 2) {
         std::vector<MgLevel> lv2;
         make_mg_levels(L, st, 3, 200, lv2);
@@ -371,6 +373,49 @@ int main(int argc, char **argv)
         }
         rel2 = std::sqrt(d2 / n2);
         n_exp1 = T.n_exp[1];
+        // the device operators of the coarse levels small enough for a dense test
+        // (interior rows from wint, explicit rows from wexp, entries below the drop
+        // threshold lumped into the diagonal): symmetric and positive definite
+        for (int l = 1; l < T.nlev - 1; ++l) {
+            const int nl = T.n[l];
+            if (nl > 2500) continue;
+            std::vector<int> at((size_t)T.box[l], -1);
+            for (int q = 0; q < nl; ++q) at[(size_t)T.pts[l][q]] = q;
+            std::vector<double> M((size_t)nl * nl, 0.0);
+            for (int q = 0; q < nl; ++q)
+                for (int k = 0; k < T.K[l]; ++k) {
+                    const int kd = T.kd[l][k];
+                    const long long o = T.pts[l][q] + ((long long)((kd & 7) - 2) * T.Bp[l][1] + (((kd >> 3) & 7) - 2)) *
+                                                          T.Bp[l][2] + (((kd >> 6) & 7) - 2);
+                    const int j = (o >= 0 && o < T.box[l]) ? at[(size_t)o] : -1;
+                    const double w = q < T.n_int[l] ? T.wint[l][k] : T.wexp[l][(size_t)k * T.n_exp[l] + (q - T.n_int[l])];
+                    if (j >= 0) M[(size_t)q * nl + j] += w;
+                }
+            double am = 0.0, mm = 0.0;
+            for (int q = 0; q < nl; ++q)
+                for (int j = 0; j < nl; ++j) {
+                    am = std::fmax(am, std::fabs(M[(size_t)q * nl + j] - M[(size_t)j * nl + q]));
+                    mm = std::fmax(mm, std::fabs(M[(size_t)q * nl + j]));
+                }
+            coarse_asym = std::fmax(coarse_asym, am / mm);
+            // Cholesky of the symmetric part
+            for (int c = 0; c < nl && coarse_spd; ++c) {
+                double d = M[(size_t)c * nl + c];
+                for (int k = 0; k < c; ++k) d -= M[(size_t)c * nl + k] * M[(size_t)c * nl + k];
+                if (!(d > 0.0)) {
+                    coarse_spd = false;
+                    break;
+                }
+                d = std::sqrt(d);
+                M[(size_t)c * nl + c] = d;
+                for (int r = c + 1; r < nl; ++r) {
+                    double v = 0.5 * (M[(size_t)r * nl + c] + M[(size_t)c * nl + r]);
+                    for (int k = 0; k < c; ++k) v -= M[(size_t)r * nl + k] * M[(size_t)c * nl + k];
+                    M[(size_t)r * nl + c] = v / d;
+                }
+            }
+            ++coarse_checked;
+        }
         // level 1 in the solver's run form: runs of 4 points, interior runs from the
         // dense window, the others from wmix, against the row form of apply()
         {
@@ -532,8 +577,10 @@ int main(int argc, char **argv)
                 "\"level1_max_nnz\": %d, \"tables_levels\": %d, \"tables_pcg_iter\": %d, "
                 "\"tables_rel_diff\": %.3e, \"tables_level1_explicit\": %d, \"tables_level1_n\": %d, "
                 "\"runs_rel_diff\": %.3e, \"restrict_runs_rel_diff\": %.3e, \"restrict_runs_aligned\": %d, "
-                "\"prolong_groups_rel_diff\": %.3e, \"prolong_runs1_rel_diff\": %.3e, \"pinfo_even\": %d}\n",
+                "\"prolong_groups_rel_diff\": %.3e, \"prolong_runs1_rel_diff\": %.3e, \"pinfo_even\": %d, "
+                "\"coarse_checked\": %d, \"coarse_spd\": %d, \"coarse_asym\": %.3e}\n",
                 2 * 3 * st.ndir + 1, k0, k1, std::sqrt(d / nx), asym / amax, maxnnz, T.nlev, k2, rel2, n_exp1, T.n[1],
-                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel, pinfo1_rel, pinfo_even ? 1 : 0);
+                runs_rel, rruns_rel, aligned ? 1 : 0, pinfo_rel, pinfo1_rel, pinfo_even ? 1 : 0, coarse_checked,
+                coarse_spd ? 1 : 0, coarse_asym);
     return 0;
 }

@@ -55,5 +55,7 @@ def test_vcycle_preconditioned_cg(harness, cell, n_stcl):
     # pass D's prolongation onto the fine groups (level-1 rows from the per-group table)
     assert r["prolong_groups_rel_diff"] < 1e-6
     assert r["pinfo_even"] == 1                      # pass D reads each parents' row start as a float2
+    # the sparsified device operators of the small coarse levels stay symmetric positive definite
+    assert r["coarse_checked"] >= 1 and r["coarse_spd"] == 1 and r["coarse_asym"] < 1e-6
     # and level 2 onto the level-1 runs (pinfo1)
     assert r["prolong_runs1_rel_diff"] < 1e-6
