@@ -293,8 +293,11 @@ int exx_plan_set_schedule(exx_plan *plan, const exx_schedule *sched);
  * (the faster run counts), and keeps the fastest for the plan's later solves
  * (ties keep the earlier candidate, the order above).  `chosen` (may be NULL)
  * receives it with its time.  The FP64 path has one schedule (plain FP64 CG)
- * and returns it untimed.  cell and orb as for exx_pairs_solve (device or host
- * memory).  Errors: those of exx_pairs_solve, EXX_ERR_ARG for sample_pairs < 1. */
+ * and returns it untimed.  A sample of several waves of the persistent grid
+ * (a few times `ctas` of exx_plan_query) gives stable choices: with one wave
+ * the slowest single pair decides each time.  cell and orb as for
+ * exx_pairs_solve (device or host memory).  Errors: those of exx_pairs_solve,
+ * EXX_ERR_ARG for sample_pairs < 1. */
 int exx_plan_autotune(exx_ctx *ctx, exx_plan *plan, const exx_cell *cell, const exx_orbitals *orb, int sample_pairs,
                       exx_schedule *chosen, void *stream);
 
